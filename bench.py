@@ -1,0 +1,334 @@
+"""Benchmark of the BSE hot path: one step = pair densities + Hamiltonian + Haydock spectrum.
+
+Workload: fcc 8x8x8 k mesh, 3 valence + 4 conduction bands (dim 6144), ~301 plane
+waves per sphere, 32^3 grid, 300 Haydock steps, 2000 frequencies, eta 0.05 eV
+(synthetic inputs of the paper's bulk BSE shape).  Every input (u store 0.94 GB,
+H 302 MB, W 404 MB) is larger than the 129 MB L2, so no flush is needed between
+steps.  Multi-GPU runs are independent replicas (weak scaling); see the design doc.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BSE kernel elements/s (dim^2 per full step: pair densities + H + Haydock eps_2)"
+UNIT = "elements/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(self.path, "w")
+            idx = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", idx], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(name):
+    from synth import config_spec, generate
+    import numpy as np
+    spec = config_spec(name)
+    s = generate(spec, wdtype=np.complex64)
+    return spec, s
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1206_3518_gb300 import bse
+    from paper_1206_3518_gb300.pipeline import Forward
+
+    spec, s = make_inputs(args.config)
+    plan = bse.Plan([spec])
+    inf = plan.info(0)
+    dim = inf["dim"]
+    F = Forward(plan, 0, nsteps=spec.nsteps, nw=spec.nw)
+    coef_h = torch.as_tensor(s.coef.astype(np.complex64)).pin_memory()
+    en_h = torch.as_tensor(s.energies).pin_memory()
+    W_h = torch.as_tensor(s.W).pin_memory()
+    om_h = torch.as_tensor(s.omega).pin_memory()
+    coef, en, W, om = (coef_h.to(dev), en_h.to(dev), W_h.to(dev), om_h.to(dev))
+    stream = torch.cuda.current_stream()
+    prec = bse.BSE_PREC_BF16X3 if args.prec == "bf16x3" else bse.BSE_PREC_FP32
+
+    ev_names = ["realspace+exchange", "init", "pair_direct", "direct_contract", "spectrum"]
+
+    def step(record=None):
+        def mark(i):
+            if record is not None:
+                record[i].record(stream)
+        mark(0)
+        bse.bse_pair_densities(plan, 0, bse.BSE_PD_REALSPACE | bse.BSE_PD_EXCHANGE, coef, en, F.rho_x, F.P, None,
+                               0, 0, F.ws_pair)
+        mark(1)
+        bse.bse_build_kernel(plan, 0, bse.BSE_BK_INIT, F.rho_x, None, 0, 0, None, en, spec.delta, prec, F.H, None)
+        mark(2)
+        for q0, q1 in F.chunks:
+            bse.bse_pair_densities(plan, 0, bse.BSE_PD_DIRECT, None, None, None, None, F.rho_dir, q0, q1, F.ws_pair)
+            mark(3)
+            bse.bse_build_kernel(plan, 0, bse.BSE_BK_DIRECT, None, F.rho_dir, q0, q1, W, None, spec.delta, prec,
+                                 F.H, F.ws_kernel)
+            mark(4)
+        bse.bse_spectrum(plan, 0, F.H, F.P, spec.nsteps, om, spec.eta, F.eps2, F.ab, F.steps_done, F.ws_spec)
+        mark(5)
+
+    launches_per_step = 3 + 1 + 3 * len(F.chunks) + 1    # realspace, pair x, dipole, init, (pair d, gemm, block)*, haydock
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    bse.bse_status_read(plan)
+
+    clocks = Clocks()
+    clocks.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    stage_ms = {n: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, n in enumerate(ev_names)}
+    bse.bse_status_read(plan)
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    ms_per_step = ms / args.steps
+
+    # end to end through host buffers: inputs H2D from pinned memory, eps_2 D2H, every step
+    eps_host = torch.empty(spec.nw, dtype=torch.float64).pin_memory()
+    h2d = coef_h.numel() * 8 + en_h.numel() * 8 + W_h.numel() * 8 + om_h.numel() * 8
+    d2h = spec.nw * 8
+    e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        coef.copy_(coef_h, non_blocking=True)
+        en.copy_(en_h, non_blocking=True)
+        W.copy_(W_h, non_blocking=True)
+        om.copy_(om_h, non_blocking=True)
+        step()
+        eps_host.copy_(F.eps2, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e_steps
+
+    peaks, src = _peaks()
+    # dominant stage: by measured time
+    dom = max(stage_ms, key=stage_ms.get)
+    roof = roofline(dom, stage_ms[dom], spec, inf, peaks, src, len(F.chunks))
+    out = {
+        "metric": METRIC, "value": world * dim * dim / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 contractions, f64 recurrence" if prec == 0 else
+        "bf16x3 contractions, f64 recurrence", "data": "synthetic",
+        "config": {"workload": f"{spec.name}: fcc a=10 bohr, 8x8x8 k, 3v4c, dim {dim}, Ecut 8.6 Ha "
+                               f"(ng_max {inf['ng_max']}), grid 32^3, {spec.nsteps} Haydock steps, {spec.nw} w",
+                   "dim": dim, "nblocks": inf["nblocks"], "precision": args.prec,
+                   "l2": "inputs larger than L2 (u 0.94 GB, H 0.30 GB, W 0.40 GB); no flush",
+                   "parallelism": f"replicas x{world}"},
+        "stages_ms": stage_ms,
+        "kernel_elements_per_s": dim * dim / ((ms_per_step - stage_ms["spectrum"]) / 1e3),
+        "spectra_per_s": 1e3 / stage_ms["spectrum"],
+        "roofline": roof, "clocks": ck,
+        "e2e": {"value": world * dim * dim / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(spec, s, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def roofline(stage, ms, spec, inf, peaks, src, nchunks):
+    """Algorithmic work of the dominant stage per launch over its measured mean duration."""
+    dim = inf["dim"]
+    nb = inf["nblocks"]
+    n1, n2, n3 = spec.fft
+    if stage == "pair_direct":
+        import math
+        nr = n1 * n2 * n3
+        products = nb * (spec.nv ** 2 + spec.nc ** 2)
+        flops = products * 5.0 * nr * math.log2(nr) / nchunks
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        return {"bound": "alu", "kernel": "pair_kernel", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / peak,
+                "work": "5 N_r log2 N_r FP32 flops per pair-density FFT (FFT convention)", "traffic": None,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"}
+    if stage == "spectrum":
+        bytes_ = spec.nsteps * 8.0 * dim * dim
+        ach = bytes_ / (ms / 1e3) / 1e9
+        return {"bound": "hbm", "kernel": "haydock_kernel", "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "work": "8 dim^2 bytes of H per Haydock step",
+                "traffic": None, "peak_source": src}
+    if stage == "direct_contract":
+        w = min(spec.nv ** 2, spec.nc ** 2)
+        ng = inf["ng_max"]
+        flops = 8.0 * (nb * w * ng * ng + nb * spec.nv ** 2 * spec.nc ** 2 * ng) / nchunks
+        ach = flops / (ms / 1e3) / 1e12
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        return {"bound": "alu", "kernel": "gemm_wr", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "work": "8 flops per complex MAC of W.R and the block products",
+                "traffic": None, "peak_source": "derived FP32 CUDA-core peak"}
+    return {"bound": "hbm", "kernel": stage, "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": None, "traffic": None}
+
+
+def cpu_baseline(spec, s, budget_s=20.0):
+    """The oracle as it stands on the host cores, on a bounded sample scaled to one full step."""
+    import numpy as np
+    import time as _t
+    from oracle import geometry as geo, kernel as ok, pair as op, spectrum as osp
+    cores = os.cpu_count()
+    blocks = geo.upper_blocks(spec)
+    rng = np.random.default_rng(0)
+    t0 = _t.perf_counter()
+    nsample = 0
+    for idx in rng.permutation(len(blocks)):
+        ik, ik2 = blocks[idx]
+        iq, rv, rc = op.direct_rho_block(spec, ik, ik2, s.gk, s.coef)
+        ok.direct_block(spec, rv, rc, ok.w_of_q(spec, s.W, iq))
+        nsample += 1
+        if _t.perf_counter() - t0 > 0.6 * budget_s:
+            break
+    t_block = (_t.perf_counter() - t0) / nsample
+    # Haydock: a few steps of the oracle recursion on a dense Hermitian matrix of the same size
+    dim = spec.dim
+    m = (rng.standard_normal((dim, dim)) + 1j * rng.standard_normal((dim, dim))).astype(np.complex128)
+    Hs = 0.5 * (m + m.conj().T)
+    P = rng.standard_normal(dim) + 0j
+    nst = 4
+    t1 = _t.perf_counter()
+    osp.haydock(Hs, P, nst)
+    t_hay = (_t.perf_counter() - t1) / nst
+    t_step = t_block * len(blocks) + t_hay * spec.nsteps
+    return {"value": dim * dim / t_step, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nsample} random upper (k,k') blocks (pair densities by correlation + K^d) and {nst} Haydock "
+                      f"steps at dim {dim}, scaled to {len(blocks)} blocks + {spec.nsteps} steps",
+            "est_step_s": t_step}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    spec, s = make_inputs(args.config)
+    times = []
+    base = None
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        base = cpu_baseline(spec, s, budget_s=args.cpu_budget)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    out = {"metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": base["est_step_s"] * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"{spec.name} (oracle, bounded sample per step)"},
+           "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "sample": base["sample"], "value": base["value"]},
+           "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="fcc_8x8x8_3v4c")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * bse.h - C ABI of the GB300 (sm_103a) plane-wave Bethe-Salpeter hot path.
+ *
+ * The path (Yan, Jacobsen & Thygesen, "Optical properties of bulk
+ * semiconductors and graphene/boron nitride", Sec. II C, Sec. III A and
+ * Appendix A) computes, for one or more periodic systems:
+ *
+ *   A0  plane-wave spheres, q folding, e-h pair and block tables (host)
+ *   A1  u_nk(r) = sum_G c_nk(G) exp(iG.r) on the real-space grid       (Eq. pair_density)
+ *   A2  rho_nm^{kk'}(G) by FFT of conj(u_nk) u_mk' pruned to the sphere (Eq. pair_density)
+ *   A3  K^x = rho_x^H diag(vbar) rho_x / (Omega Nk)                   (Eq. V_eh, G = 0 dropped)
+ *   A4  K^d = rho_vv'^H W(q) rho_cc' / (Omega Nk) per (k,k') block      (Eq. W_SS)
+ *   A5  H = diag(e_c + Delta - e_v) + 2 K^x - K^d  (TDA, Eq. kernel)
+ *   A6  k.p dipole P_S (Eq. density_matrix)
+ *   A7  Haydock/Lanczos recursion on H from P (FP64 recurrence)
+ *   A8  eps_2(w) = -C |P|^2 Im g(w + i eta), C = 8 pi/(Omega Nk)     (Eq. epsilon_chi_bar)
+ *   A9  adjoint of a spectral loss w.r.t. Delta, W and the pair densities
+ *
+ * Conventions (all entry points):
+ *  - Hartree atomic units.  Complex single = interleaved float2 (re, im),
+ *    complex double = interleaved double2.
+ *  - Every pointer argument except the plan, the info structs and the
+ *    explicitly host arrays is a DEVICE pointer owned by the caller; the
+ *    library never frees caller memory and never allocates after
+ *    bse_plan_create.  Scratch comes from a caller-allocated workspace whose
+ *    size bse_workspace_size reports.
+ *  - Calls enqueue work on the given stream and return without a host
+ *    synchronisation; errors detected on the host are returned at once,
+ *    errors detected on the device land in the plan's device status word and
+ *    are returned by bse_status_read (which synchronises the stream).
+ *  - Every function returns a bse_status; bse_last_error() gives a
+ *    thread-local message for the last non-OK status.
+ *  - Systems inside one plan are addressed by index s in [0, nsys).
+ */
+#ifndef BSE_H
+#define BSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BSE_OK = 0,
+  BSE_ERR_ARG = 1,          /* invalid argument, shape or size */
+  BSE_ERR_CUDA = 2,         /* CUDA runtime error (message in bse_last_error) */
+  BSE_ERR_NONFINITE = 3,    /* NaN/Inf found in an input scan */
+  BSE_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+  BSE_ERR_UNSUPPORTED = 5,  /* configuration outside the compiled kernels */
+  BSE_ERR_WORKSPACE = 6     /* workspace smaller than bse_workspace_size */
+} bse_status;
+
+typedef enum { BSE_LATTICE_FCC = 0, BSE_LATTICE_HEX = 1 } bse_lattice;
+typedef enum { BSE_COULOMB_3D = 0, BSE_COULOMB_SLAB = 1 } bse_coulomb;
+typedef enum { BSE_PREC_FP32 = 0, BSE_PREC_BF16X3 = 1 } bse_precision;
+
+/* Workspace kinds for bse_workspace_size. */
+typedef enum {
+  BSE_WS_PAIR = 0,      /* bse_pair_densities: real-space wavefunctions u_nk(r) */
+  BSE_WS_KERNEL = 1,    /* bse_build_kernel: W.rho products of one q chunk */
+  BSE_WS_SPECTRUM = 2,  /* bse_spectrum: Krylov basis, vectors, partial sums */
+  BSE_WS_BACKWARD = 3   /* bse_spectrum_backward: basis, dL/dH, chain products */
+} bse_ws_kind;
+
+/* Stage flags for bse_pair_densities and bse_build_kernel. */
+#define BSE_PD_REALSPACE 1u   /* A1: fill u_nk(r) in the workspace            */
+#define BSE_PD_EXCHANGE  2u   /* A2 exchange set rho_x and the A6 dipole P     */
+#define BSE_PD_DIRECT    4u   /* A2 direct set rho_vv', rho_cc' of a q range   */
+#define BSE_BK_INIT      1u   /* A3 + A5 diagonal: H = diag + 2 K^x (upper)    */
+#define BSE_BK_DIRECT    2u   /* A4 + A5: H -= K^d for a q range, mirror       */
+
+/*
+ * One periodic system.  Lattices: fcc with conventional constant a
+ * (a_i = a/2 {(0,1,1),(1,0,1),(1,1,0)}), or a hexagonal sheet a_1 = a(1,0,0),
+ * a_2 = a(-1/2, sqrt3/2, 0), a_3 = (0,0,c).  k mesh Gamma-centred,
+ * k = sum_j (i_j/nk_j) b_j, ik = (i1*nk2 + i2)*nk3 + i3; fcc needs
+ * nk1 = nk2 = nk3, hex needs nk1 = nk2 and nk3 = 1.  The q mesh is the k mesh
+ * (Sec. III A).  Spheres: |k+G|^2/2 <= ecut (wavefunctions) and |q+G|^2/2 <= ecut
+ * (pair densities, W), ordered by exact key then g1, g2, g3.
+ */
+typedef struct {
+  int lattice;          /* bse_lattice */
+  double a;             /* bohr */
+  double c;             /* bohr, hex out-of-plane period (ignored for fcc) */
+  int nk[3];
+  int nv, nc;           /* valence / conduction bands kept (TDA pair basis) */
+  double ecut;          /* Ha */
+  int fft[3];           /* real-space grid; each a divisor of 192 (2^a 3^b, b <= 1), <= 64 */
+  int coulomb;          /* bse_coulomb: 3D 4pi/|G|^2 or slab-truncated 2D */
+  double qhat[3];       /* optical-limit direction (Cartesian, normalised by the library) */
+  double gap_floor;     /* Ha, floor of e_c - e_v in the dipole denominator */
+} bse_system;
+
+/* Sizes and strides of system s (filled by bse_plan_info). */
+typedef struct {
+  int nkpt, nb, dim;          /* dim = nkpt*nv*nc, pair index S = (ik*nv + iv)*nc + ic */
+  int npw_max;                /* coefficient row stride (max sphere size over k) */
+  int ng_max;                 /* W row stride and pair-density vector stride */
+  int ng0;                    /* size of the q = 0 sphere (exchange set) */
+  int nq;                     /* = nkpt */
+  long long nblocks;          /* upper (k <= k') blocks */
+  double omega_cell;          /* bohr^3 */
+  double norm;                /* 1/(Omega Nk) */
+  double prefactor;           /* C = 8 pi/(Omega Nk) */
+} bse_info;
+
+typedef struct bse_plan bse_plan;
+
+/* Thread-local message of the last failing call (never NULL). */
+const char* bse_last_error(void);
+
+/*
+ * A0.  Build host tables for nsys systems (Sec. II C plane-wave sets, Sec.
+ * III A q mesh and G0 folding), upload them, and allocate the plan's small
+ * device tables on the current device.  Errors: BSE_ERR_ARG for an invalid
+ * system (lattice/mesh mismatch, grid not 2^a 3^b or too small for alias-free
+ * pair densities: N_i > 2 Fwf_i + Fpair_i), BSE_ERR_CUDA on allocation
+ * failure.  The plan is bound to the device current at creation.
+ */
+bse_status bse_plan_create(const bse_system* sys, int nsys, bse_plan** out);
+
+/*
+ * A0 on the host only: the same tables without any device allocation (no GPU
+ * needed).  Such a plan serves bse_plan_info, the table exports and
+ * bse_workspace_size / bse_rho_dir_count; compute calls return BSE_ERR_ARG.
+ */
+bse_status bse_plan_create_host(const bse_system* sys, int nsys, bse_plan** out);
+bse_status bse_plan_destroy(bse_plan* plan);
+bse_status bse_plan_info(const bse_plan* plan, int s, bse_info* info);
+
+/*
+ * Test exports of the bit-exact host tables (host buffers).
+ * bse_gvectors: sphere of k (is_q = 0) or q (is_q = 1) of mesh index kq as
+ * int32 [n][3] reduced G; pass out = NULL to query n.
+ * bse_pair_blocks: the upper blocks of q-index iq in processing order as
+ * int32 [n][2] (ik, ik'), plus G0 of each block as int32 [n][3]; out/g0 may be
+ * NULL to query n.
+ */
+bse_status bse_gvectors(const bse_plan* plan, int s, int kq, int is_q, int32_t* out, int* n);
+bse_status bse_pair_blocks(const bse_plan* plan, int s, int iq, int32_t* out, int32_t* g0, int* n);
+
+/*
+ * Workspace bytes for one call kind on system s.  For BSE_WS_KERNEL, arg is
+ * the largest q chunk (q_end - q_begin) that will be passed; for
+ * BSE_WS_SPECTRUM and BSE_WS_BACKWARD, arg is nsteps.  Ignored otherwise.
+ */
+bse_status bse_workspace_size(const bse_plan* plan, int s, int kind, long long arg, size_t* bytes);
+
+/* Number of complex vectors of rho_dir for q in [q_begin, q_end) (each ng_max long). */
+bse_status bse_rho_dir_count(const bse_plan* plan, int s, int q_begin, int q_end, long long* nvec);
+
+/*
+ * A1 + A2 (+ A6).  Pair densities by batched 3D FFT (Eq. pair_density):
+ *   rho_nm^{kk'}(G) = (1/N_r) sum_r conj(u_nk(r)) u_mk'(r) exp(-iG.r).
+ * coef     complex64 [nkpt][nb][npw_max], c_nk(G) in sphere order (zero padded).
+ * energies float64  [nkpt][nb], bands ascending (valence first), Ha.
+ * rho_x    complex64 [dim][ng_max]: rho_vc^{kk}(G) on the q = 0 sphere (S = (k,v,c)).
+ * P        complex128 [dim]: P_S = conj(qhat.sum_G conj(c_vk)(k+G)c_ck)/max(e_c-e_v, gap_floor).
+ * rho_dir  complex64 [nvec][ng_max] for q in [q_begin, q_end): per q, first the
+ *          nblk_q*nv*nv vectors rho~_vv'^{kk'} (block-major, then v, v'), then the
+ *          nblk_q*nc*nc vectors rho~_cc'^{kk'}; entry p is taken at G = g_p(q) - G0,
+ *          g_p the p-th vector of the q sphere, so q_unf + G = q + g_p.
+ * flags    BSE_PD_* stages; REALSPACE must run (once) before the others, with
+ *          the same workspace.  Unused outputs may be NULL.
+ * Errors: BSE_ERR_ARG (range, NULL for a requested output), BSE_ERR_WORKSPACE.
+ */
+bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags,
+                              const void* coef, const double* energies,
+                              void* rho_x, void* P,
+                              void* rho_dir, int q_begin, int q_end,
+                              void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * A3 - A5.  Hamiltonian in the TDA (Eq. kernel, Eqs. V_eh and W_SS):
+ *   H = diag(e_ck + delta - e_vk) + 2 K^x - K^d.
+ * BSE_BK_INIT writes diag + 2K^x on the upper block triangle (k <= k').
+ * BSE_BK_DIRECT subtracts K^d for the upper blocks of q in [q_begin, q_end)
+ * (rho_dir laid out as in bse_pair_densities for the same range) and writes the
+ * mirrored lower block H_k'k = H_kk'^H; diagonal blocks become (B + B^H)/2.
+ * After INIT and DIRECT over all q, H is the full Hermitian matrix.
+ * W        complex64 [nq][ng_max][ng_max], W_q[p][p'] Hermitian, including 4 pi.
+ * H        complex64 [dim][dim] row-major.
+ * prec     BSE_PREC_FP32 (CUDA-core FP32) or BSE_PREC_BF16X3 (tcgen05 BF16
+ *          hi/lo split products, FP32 accumulation) for the contractions.
+ * Errors: BSE_ERR_ARG, BSE_ERR_UNSUPPORTED (precision not built), BSE_ERR_WORKSPACE.
+ */
+bse_status bse_build_kernel(bse_plan* plan, int s, unsigned flags,
+                            const void* rho_x, const void* rho_dir, int q_begin, int q_end,
+                            const void* W, const double* energies, double delta, int prec,
+                            void* H, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Y = H X for nvec vectors (X, Y complex128 [nvec][dim]); H complex64 products
+ * accumulated in FP32 within 16-element chunks and combined in FP64.
+ */
+bse_status bse_apply_H(bse_plan* plan, int s, const void* H, const void* X, void* Y, int nvec,
+                       void* stream);
+
+/*
+ * A7 + A8.  Haydock recursion (Lanczos from v_0 = P/|P|, classical
+ * Gram-Schmidt applied twice against the whole basis each step, FP64) and
+ * eps_2(w) = -C |P|^2 Im g(w + i eta) with the continued fraction
+ * g(z) = 1/(z - a_0 - b_1^2/(z - a_1 - ...)), no terminator
+ * (Eq. epsilon_chi_bar in the TDA, Appendix A resolvent).
+ * omega float64 [nw] (Ha), eps2 float64 [nw], ab float64 [2*nsteps]
+ * (a_0..a_{n-1}, then b_0 = 0, b_1..b_{n-1}), steps_done int32 [1]: fewer than
+ * nsteps after a breakdown (b_{j+1} <= 1e-10 |H v_j|), which is exact, not an
+ * error.  One persistent cooperative launch; device-side barrier waits are
+ * bounded and report BSE_ERR_TIMEOUT through bse_status_read.
+ */
+bse_status bse_spectrum(bse_plan* plan, int s, const void* H, const void* P, int nsteps,
+                        const double* omega, int nw, double eta,
+                        double* eps2, double* ab, int* steps_done,
+                        void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * A9.  Adjoint of L(eps_2) given dL_deps2 float64 [nw].  Recomputes the
+ * Lanczos basis, forms G_H = -C sum_w g(w) i xt(w) x(w)^H from the Krylov
+ * resolvent (x = R(z)P, xt = R(conj z)P), and chains it:
+ *   dL_ddelta float64 [1]  = Re tr G_H,
+ *   dL_dH     complex64 [dim][dim] (optional, may be NULL: then kept in ws),
+ *   dL_drho_x complex64 [dim][ng_max], dL_drho_dir as rho_dir for all q,
+ *   dL_dW     complex64 [nq][ng_max][ng_max],
+ * each stored entry taken as a free variable; complex gradients are
+ * dL/dRe + i dL/dIm.  Any of dL_drho_x, dL_drho_dir, dL_dW may be NULL.
+ */
+bse_status bse_spectrum_backward(bse_plan* plan, int s, const void* H, const void* P, int nsteps,
+                                 const double* omega, int nw, double eta, const double* dL_deps2,
+                                 const void* rho_x, const void* rho_dir, const void* W,
+                                 double* dL_ddelta, void* dL_dH, void* dL_drho_x,
+                                 void* dL_drho_dir, void* dL_dW,
+                                 void* ws, size_t ws_bytes, void* stream);
+
+/* Synchronise the stream and return (then clear) the plan's device status word. */
+bse_status bse_status_read(bse_plan* plan, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSE_H */

@@ -1,0 +1,253 @@
+// Kernel contractions and Hamiltonian assembly, CUDA-core FP32 form (steps A3-A5).
+//
+// Eq. kernel (TDA, singlet):  H = diag(e_c + Delta - e_v) + 2 K^x - K^d
+//   K^x_SS' = (1/(Omega Nk)) sum_{G != 0} conj(rho_vc^{kk}(G)) vbar(G) rho_v'c'^{k'k'}(G)   (Eq. V_eh)
+//   K^d_SS' = (1/(Omega Nk)) sum_{G,G'} conj(rho_vv'^{kk'}(G)) W_GG'(q) rho_cc'^{kk'}(G')  (Eq. W_SS)
+//
+// init_kernel   : 2K^x + diag on every tile that touches the upper block triangle; the
+//                 exchange scale sqrt(2 vbar/(Omega Nk)) is applied to both operands.
+// gemm_wr       : per q, X = W(q) R for the smaller band side (grouped over the q chunk),
+//                 stored as X^T rows [col][G] (G contiguous).
+// block_kernel  : per upper block (k <= k'), M = X^H R of the other side (K = NG_q),
+//                 H_kk' = H_kk' - M/(Omega Nk) and the mirror H_k'k = H_kk'^H;
+//                 diagonal blocks become (B + B^H)/2.
+// All three GEMM-like steps use one tiled FP32 complex "NT" core: C[m][n] =
+// sum_k opA(A[m][k]) B[n][k] with both operands K-contiguous.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace bse {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, kGemmThreads = 256;
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// One 64x64 output tile of C = opA(A) B^T over K, accumulated in registers (4x4 per thread).
+// A: [M][lda], B: [N][ldb] float2, K-contiguous.  Optional per-k scale applied to both.
+template <bool CONJ_A, bool SCALE>
+__device__ __forceinline__ void tile_nt(const float2* __restrict__ A, int lda, int M, const float2* __restrict__ B,
+                                        int ldb, int N, int K, const float* __restrict__ kscale, int m0, int n0,
+                                        float2 (&acc)[4][4]) {
+  __shared__ float2 As[BK][BM + 1];
+  __shared__ float2 Bs[BK][BN + 1];
+  const int t = threadIdx.x;
+  const int lk = t % BK, lr = t / BK;          // loader: 16 rows x 16 k per pass
+  const int tm = t / 16, tn = t % 16;          // compute: rows tm*4.., cols tn*4..
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    const int kk = k0 + lk;
+    const float sc = (SCALE && kk < K) ? kscale[kk] : 1.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = lr + 16 * i;
+      float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+      if (kk < K && m0 + r < M) a = A[(size_t)(m0 + r) * lda + kk];
+      if (kk < K && n0 + r < N) b = B[(size_t)(n0 + r) * ldb + kk];
+      if (CONJ_A) a.y = -a.y;
+      if (SCALE) {
+        a.x *= sc; a.y *= sc;
+        b.x *= sc; b.y *= sc;
+      }
+      As[lk][r] = a;
+      Bs[lk][r] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      float2 av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[k][tm * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tn * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fmaf(av[i].x, bv[j].x, fmaf(-av[i].y, bv[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(av[i].x, bv[j].y, fmaf(av[i].y, bv[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int kpt_of_pair(const DevSys& d, int S) { return S / (d.nv * d.nc); }
+
+// H[S][S'] = 2 K^x + delta_SS' (e_c + Delta - e_v) on tiles touching k(S) <= k(S').
+__global__ __launch_bounds__(kGemmThreads) void init_kernel(DevSys d, const float2* __restrict__ rho_x,
+                                                            const double* __restrict__ e, double delta,
+                                                            float2* __restrict__ H) {
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  if (m0 >= d.dim || n0 >= d.dim) return;
+  const int mlast = min(m0 + BM, d.dim) - 1;
+  if (kpt_of_pair(d, m0) > kpt_of_pair(d, min(n0 + BN, d.dim) - 1)) return;   // strictly lower block triangle
+  (void)mlast;
+  float2 acc[4][4];
+  tile_nt<true, true>(rho_x, d.ng_max, d.dim, rho_x, d.ng_max, d.dim, d.ng0, d.xscale, m0, n0, acc);
+  const int tm = threadIdx.x / 16, tn = threadIdx.x % 16;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int S = m0 + tm * 4 + i;
+    if (S >= d.dim) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int S2 = n0 + tn * 4 + j;
+      if (S2 >= d.dim) continue;
+      float2 v = acc[i][j];
+      if (S == S2) {
+        const int ic = S % d.nc, iv = (S / d.nc) % d.nv, k = S / (d.nv * d.nc);
+        v.x += (float)(e[(size_t)k * d.nb + d.nv + ic] + delta - e[(size_t)k * d.nb + iv]);
+      }
+      H[(size_t)S * d.dim + S2] = v;
+    }
+  }
+}
+
+// Grouped over the q chunk: X_q^T[col][G] = sum_G' R_q[col][G'] W_q[G][G']  (W Hermitian).
+__global__ __launch_bounds__(kGemmThreads) void gemm_wr(DevSys d, const float2* __restrict__ rho_dir,
+                                                       const float2* __restrict__ W, float2* __restrict__ X,
+                                                       int q_begin, long long vbase, int side_c) {
+  const int q = q_begin + blockIdx.z;
+  const long long b0 = d.qblk_off[q_begin];
+  const long long nblk = d.qblk_off[q + 1] - d.qblk_off[q];
+  const int w = side_c ? d.nc * d.nc : d.nv * d.nv;
+  const int M = (int)(nblk * w), NG = d.ngq[q];
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  if (m0 >= M || n0 >= NG) return;
+  long long aoff = d.qvec_off[q] - vbase;
+  if (side_c) aoff += nblk * d.nv * d.nv;
+  const float2* A = rho_dir + (size_t)aoff * d.ng_max;
+  const float2* B = W + (size_t)q * d.ng_max * d.ng_max;
+  float2* C = X + (size_t)((d.qblk_off[q] - b0) * w) * d.ng_max;
+  float2 acc[4][4];
+  tile_nt<false, false>(A, d.ng_max, M, B, d.ng_max, NG, NG, nullptr, m0, n0, acc);
+  const int tm = threadIdx.x / 16, tn = threadIdx.x % 16;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = m0 + tm * 4 + i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = n0 + tn * 4 + j;
+      if (c < NG) C[(size_t)r * d.ng_max + c] = acc[i][j];
+    }
+  }
+}
+
+constexpr int kBlkThreads = 256, KC = 32;
+
+// Per upper block: M[a][c] = sum_G conj(L[a][G]) Rr[c][G], a = (v,v'), c = (c,c');
+// side V: L = X (= W R_v), Rr = R_c;  side C: L = R_v, Rr = X (= W R_c).
+__global__ __launch_bounds__(kBlkThreads) void block_kernel(DevSys d, const float2* __restrict__ rho_dir,
+                                                           const float2* __restrict__ X, float2* __restrict__ H,
+                                                           int q_begin, long long vbase, int side_c) {
+  __shared__ float2 Ls[16][KC + 1];
+  __shared__ float2 Rs[16][KC + 1];
+  __shared__ float2 Bs[16][17];
+  const long long b0 = d.qblk_off[q_begin];
+  const long long b = b0 + blockIdx.x;
+  const int4 blk = d.blocks[b];
+  const int k = blk.x, k2 = blk.y, q = blk.z;
+  const long long qb = d.qblk_off[q];
+  const long long nblk = d.qblk_off[q + 1] - qb;
+  const long long local = b - qb;
+  const int nv2 = d.nv * d.nv, nc2 = d.nc * d.nc;
+  const long long vbase_q = d.qvec_off[q] - vbase;
+  const float2* Rv = rho_dir + (size_t)(vbase_q + local * nv2) * d.ng_max;
+  const float2* Rc = rho_dir + (size_t)(vbase_q + nblk * nv2 + local * nc2) * d.ng_max;
+  const int w = side_c ? nc2 : nv2;
+  const float2* Xb = X + (size_t)((qb - b0 + local) * w) * d.ng_max;
+  const float2* L = side_c ? Rv : Xb;
+  const float2* R = side_c ? Xb : Rc;
+  const int NG = d.ngq[q];
+  const int t = threadIdx.x;
+  const int a = t / nc2, c = t % nc2;
+  const bool active = t < nv2 * nc2;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int g0 = 0; g0 < NG; g0 += KC) {
+    for (int i = t; i < 16 * KC; i += kBlkThreads) {
+      const int r = i / KC, g = i % KC;
+      const bool in = (g0 + g) < NG;
+      Ls[r][g] = (r < nv2 && in) ? L[(size_t)r * d.ng_max + g0 + g] : make_float2(0.f, 0.f);
+      Rs[r][g] = (r < nc2 && in) ? R[(size_t)r * d.ng_max + g0 + g] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll 8
+      for (int g = 0; g < KC; ++g) {
+        const float2 l = Ls[a][g], r = Rs[c][g];
+        acc.x = fmaf(l.x, r.x, fmaf(l.y, r.y, acc.x));     // conj(l) r
+        acc.y = fmaf(l.x, r.y, fmaf(-l.y, r.x, acc.y));
+      }
+    }
+    __syncthreads();
+  }
+  const int nv = d.nv, nc = d.nc, nvc = nv * nc;
+  const float nrm = (float)d.norm;
+  int row = 0, col = 0;
+  float2 val = make_float2(0.f, 0.f);
+  if (active) {
+    const int v = a / nv, vp = a % nv, cc = c / nc, cp = c % nc;
+    row = v * nc + cc;                 // (k, v, c) local
+    col = vp * nc + cp;                // (k', v', c') local
+    const size_t hij = (size_t)(k * nvc + row) * d.dim + (size_t)k2 * nvc + col;
+    const float2 h = H[hij];
+    val = make_float2(h.x - nrm * acc.x, h.y - nrm * acc.y);
+    if (k != k2) {
+      H[hij] = val;
+      H[(size_t)(k2 * nvc + col) * d.dim + (size_t)k * nvc + row] = make_float2(val.x, -val.y);
+    } else {
+      Bs[row][col] = val;
+    }
+  }
+  if (k == k2) {
+    __syncthreads();
+    if (active) {
+      const float2 o = Bs[col][row];
+      H[(size_t)(k * nvc + row) * d.dim + (size_t)k * nvc + col] =
+          make_float2(0.5f * (val.x + o.x), 0.5f * (val.y - o.y));
+    }
+  }
+}
+
+}  // namespace
+
+size_t kernel_ws_bytes(const DevSys& d, long long qchunk) {
+  const long long w = (d.nv * d.nv <= d.nc * d.nc) ? d.nv * d.nv : d.nc * d.nc;
+  long long nb = qchunk * d.nkpt;
+  if (nb > d.nblocks) nb = d.nblocks;
+  return (size_t)(nb * w) * d.ng_max * sizeof(float2);
+}
+
+int launch_kernel_init(const DevSys& d, const void* rho_x, const double* energies, double delta, void* H,
+                       void* stream) {
+  dim3 grid((d.dim + BN - 1) / BN, (d.dim + BM - 1) / BM);
+  init_kernel<<<grid, kGemmThreads, 0, (cudaStream_t)stream>>>(d, (const float2*)rho_x, energies, delta, (float2*)H);
+  return (int)cudaGetLastError();
+}
+
+int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long b_begin,
+                               long long b_count, long long vbase, long long max_rows, const void* W, int prec,
+                               void* H, void* ws, void* stream) {
+  if (prec != BSE_PREC_FP32) return -1;
+  const int side_c = (d.nc * d.nc < d.nv * d.nv) ? 1 : 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  dim3 grid((d.ng_max + BN - 1) / BN, (unsigned)((max_rows + BM - 1) / BM), q_end - q_begin);
+  gemm_wr<<<grid, kGemmThreads, 0, st>>>(d, (const float2*)rho_dir, (const float2*)W, (float2*)ws, q_begin, vbase,
+                                         side_c);
+  int e = (int)cudaGetLastError();
+  if (e) return e;
+  if (b_count > 0)
+    block_kernel<<<(unsigned)b_count, kBlkThreads, 0, st>>>(d, (const float2*)rho_dir, (const float2*)ws, (float2*)H,
+                                                            q_begin, vbase, side_c);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace bse

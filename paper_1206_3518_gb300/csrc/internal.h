@@ -1,0 +1,81 @@
+// Internal declarations shared by the host planner, the C-ABI glue and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <vector_types.h>
+#include <string>
+#include <vector>
+
+#include "bse.h"
+
+namespace bse {
+
+constexpr double kPi = 3.141592653589793;
+
+// Device-side description of one system: pointers into the plan's device tables.
+struct DevSys {
+  int nkpt, nb, nv, nc, dim, npw_max, ng_max, ng0, nq;
+  int n1, n2, n3;                 // FFT grid
+  int nk1, nk2, nk3;              // k mesh
+  int fwf[3], fpair[3];           // max |g| per axis of wavefunction / pair spheres (after G0)
+  double norm, prefactor, omega_cell;
+  const char4* gk;                // [nkpt][npw_max]  (g1,g2,g3,0) of the k spheres
+  const int* npw;                 // [nkpt]
+  const char4* gq;                // [nq][ng_max]      (g1,g2,g3,0) of the q spheres
+  const int* ngq;                 // [nq]
+  const int4* blocks;             // [nblocks] (ik, ik2, iq, g0 packed as (g0+1) bits)
+  const long long* qblk_off;      // [nq+1] first block of each q (blocks sorted by q, then ik)
+  const long long* qvec_off;      // [nq+1] first rho_dir vector of each q
+  const double* kgq;              // [nkpt][npw_max] qhat.(k+G), Cartesian
+  const float* xscale;            // [ng_max] sqrt(2 vbar(G) / (Omega Nk)), 0 at G = 0 and beyond ng0
+  long long nblocks;
+};
+
+struct SysPlan {
+  bse_system sys;
+  DevSys d;                       // device view (pointers valid on the plan's device)
+  std::vector<std::vector<int32_t>> gk, gq;   // host spheres, flattened (g1,g2,g3)*
+  std::vector<int32_t> blocks;                 // host (ik, ik2, iq, g0x, g0y, g0z) per block
+  std::vector<long long> qblk_off, qvec_off;
+  void* dmem = nullptr;           // one device allocation holding every table
+};
+
+}  // namespace bse
+
+struct bse_plan {
+  int device = 0;
+  std::vector<bse::SysPlan> sys;
+  int* d_status = nullptr;        // device status word (bse_status of the first device-side error)
+};
+
+namespace bse {
+bse_status set_error(bse_status st, const std::string& msg);
+bse_status cuda_check(int err, const char* what);
+
+// Kernel launchers (defined in the .cu files); all return cudaError_t as int.
+int launch_realspace(const DevSys& d, const void* coef, void* u, void* stream);
+int launch_pair_exchange(const DevSys& d, const void* u, void* rho_x, void* stream);
+int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, long long b_begin, long long b_count,
+                       long long vbase, void* stream);
+int launch_dipole(const DevSys& d, const void* coef, const double* energies, double gap_floor, void* P, void* stream);
+int pair_supported(const DevSys& d);
+
+int launch_kernel_init(const DevSys& d, const void* rho_x, const double* energies, double delta, void* H, void* stream);
+int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long b_begin,
+                               long long b_count, long long vbase, long long max_rows, const void* W, int prec,
+                               void* H, void* ws, void* stream);
+size_t kernel_ws_bytes(const DevSys& d, long long qchunk);
+
+int launch_apply_h(const DevSys& d, const void* H, const void* X, void* Y, int nvec, void* stream);
+size_t spectrum_ws_bytes(const DevSys& d, long long nsteps);
+int launch_spectrum(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw,
+                    double eta, double* eps2, double* ab, int* steps_done, void* ws, int* status, void* stream);
+size_t backward_ws_bytes(const DevSys& d, long long nsteps);
+int launch_backward(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw,
+                    double eta, const double* dL, const void* rho_x, const void* rho_dir, const void* W,
+                    double* d_delta, void* dH, void* drho_x, void* drho_dir, void* dW, void* ws, int* status,
+                    void* stream);
+int upload_twiddles();
+int run_haydock(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw, double eta,
+                double* eps2, double* ab, int* steps_done, void* ws, int* status, void* stream, double2** V_out);
+}  // namespace bse

@@ -1,0 +1,372 @@
+// Pair densities by batched, pruned 3D FFTs (steps A1, A2) and the k.p dipole (A6).
+//
+// Eq. pair_density: rho_nm^{kk'}(G) = <psi_nk| exp(-i(q+G).r) |psi_mk'> with k' = k + q
+// unfolded; with psi = Omega^{-1/2} exp(ik.r) u and u(r) = sum_G c(G) exp(iG.r) this is
+// (1/N_r) sum_r conj(u_nk(r)) u_mk'(r) exp(-iG.r) on an alias-free grid.
+//
+// A1 (realspace_kernel): one CTA per (k, n).  The sphere is scattered into a small
+// box of the kept frequencies, then three passes of register FFTs (x, y, z) expand
+// it onto the N1 x N2 x N3 grid; only lines that carry nonzero data are transformed.
+//
+// A2 (pair_kernel): one CTA per job = (k, k', band set n, band set m).  The grid is
+// streamed in x-slabs, ROWS z-lines at a time, for every band of the job (each
+// u_nk line read once per job and reused by all |m| products).  Per slab:
+//   stage 1: each thread forms conj(u_n) u_m along one z-line and FFTs it in
+//            registers, keeping |f3| <= F3;
+//   stage 2: y-line FFTs of the kept planes, keeping |f2| <= F2;
+//   stage 3: the x direction is a direct DFT accumulated over slabs, evaluated
+//            only at the sphere points (register accumulators).
+// Work therefore scales with the kept windows rather than with N^3 log N in the
+// last two passes.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace bse {
+namespace {
+
+__constant__ float2 c_tw[fft::kTwN];
+
+using fft::cadd;
+using fft::cconj;
+using fft::cmul;
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------- A1
+template <int N1, int N2, int N3, int F1, int F2, int F3>
+struct RsCfg {
+  static constexpr int M1 = 2 * F1 + 1, M2 = 2 * F2 + 1, M3 = 2 * F3 + 1;
+  static constexpr int GS = (N1 % 16 == 0) ? 16 : ((N1 % 12 == 0) ? 12 : ((N1 % 8 == 0) ? 8 : N1));
+  static constexpr size_t smem = sizeof(float2) * ((size_t)M1 * M2 * M3 + (size_t)N1 * M2 * M3 + (size_t)GS * N2 * M3);
+};
+
+template <int N1, int N2, int N3, int F1, int F2, int F3>
+__global__ __launch_bounds__(kThreads) void realspace_kernel(DevSys d, const float2* __restrict__ coef,
+                                                             float2* __restrict__ u) {
+  using C = RsCfg<N1, N2, N3, F1, F2, F3>;
+  constexpr int M1 = C::M1, M2 = C::M2, M3 = C::M3, GS = C::GS;
+  extern __shared__ float4 sm4[];
+  float2* box = reinterpret_cast<float2*>(sm4);
+  float2* T1 = box + M1 * M2 * M3;
+  float2* T2 = T1 + N1 * M2 * M3;
+  const int tid = threadIdx.x;
+  const int k = blockIdx.x / d.nb, n = blockIdx.x % d.nb;
+  for (int i = tid; i < M1 * M2 * M3; i += kThreads) box[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const int npw = d.npw[k];
+  for (int t = tid; t < npw; t += kThreads) {
+    const char4 g = d.gk[(size_t)k * d.npw_max + t];
+    box[((g.x + F1) * M2 + (g.y + F2)) * M3 + (g.z + F3)] = coef[((size_t)k * d.nb + n) * d.npw_max + t];
+  }
+  __syncthreads();
+  for (int it = tid; it < M2 * M3; it += kThreads) {          // x pass, nonzero (f2, f3) lines
+    float2 x[N1];
+#pragma unroll
+    for (int j = 0; j < N1; ++j) x[j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int f = -F1; f <= F1; ++f) x[(f + N1) % N1] = box[(f + F1) * M2 * M3 + it];
+    fft::line<N1, false>(c_tw, x);
+#pragma unroll
+    for (int j = 0; j < N1; ++j) T1[j * M2 * M3 + it] = x[j];
+  }
+  __syncthreads();
+  float2* dst0 = u + ((size_t)k * d.nb + n) * ((size_t)N1 * N2 * N3);
+  for (int s0 = 0; s0 < N1; s0 += GS) {
+    for (int it = tid; it < GS * M3; it += kThreads) {        // y pass on GS slabs
+      const int jj = it / M3, m3 = it % M3;
+      float2 y[N2];
+#pragma unroll
+      for (int j = 0; j < N2; ++j) y[j] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int f = -F2; f <= F2; ++f) y[(f + N2) % N2] = T1[((s0 + jj) * M2 + (f + F2)) * M3 + m3];
+      fft::line<N2, false>(c_tw, y);
+#pragma unroll
+      for (int j = 0; j < N2; ++j) T2[(jj * N2 + j) * M3 + m3] = y[j];
+    }
+    __syncthreads();
+    for (int it = tid; it < GS * N2; it += kThreads) {        // z pass, full lines written out
+      const int jj = it / N2, j2 = it % N2;
+      float2 z[N3];
+#pragma unroll
+      for (int j = 0; j < N3; ++j) z[j] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int f = -F3; f <= F3; ++f) z[(f + N3) % N3] = T2[(jj * N2 + j2) * M3 + (f + F3)];
+      fft::line<N3, false>(c_tw, z);
+      float4* dst = reinterpret_cast<float4*>(dst0 + ((size_t)(s0 + jj) * N2 + j2) * N3);
+#pragma unroll
+      for (int j = 0; j < N3 / 2; ++j) dst[j] = make_float4(z[2 * j].x, z[2 * j].y, z[2 * j + 1].x, z[2 * j + 1].y);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- A2
+template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int ACC>
+struct PairCfg {
+  static constexpr int M2 = 2 * F2 + 1, M3 = 2 * F3 + 1;
+  static constexpr int LD = N3 + 1;    // padded z-line stride in shared memory (conflict-free)
+  static size_t smem(int ng_max) {
+    return sizeof(float2) * ((size_t)BMAX * ROWS * LD + (size_t)PMAX * N2 * M3 + (size_t)PMAX * M2 * M3) +
+           sizeof(int2) * (size_t)ng_max;
+  }
+};
+
+struct Job {
+  int k, k2, n0, nn, m0, nm, q, g0x, g0y, g0z;
+  float2* out;
+};
+
+// mode 0: exchange set (one job per k: v x c at k = k', q = 0);
+// mode 1: direct set (two jobs per upper block: v x v' and c x c' on the sphere of fold(k'-k)).
+__device__ __forceinline__ Job decode_job(const DevSys& d, int mode, long long b0, long long vbase, float2* out) {
+  Job j;
+  if (mode == 0) {
+    j.k = j.k2 = blockIdx.x;
+    j.n0 = 0;
+    j.nn = d.nv;
+    j.m0 = d.nv;
+    j.nm = d.nc;
+    j.q = 0;
+    j.g0x = j.g0y = j.g0z = 0;
+    j.out = out + (size_t)blockIdx.x * d.nv * d.nc * d.ng_max;
+    return j;
+  }
+  const long long b = b0 + (blockIdx.x >> 1);
+  const int kind = blockIdx.x & 1;
+  const int4 blk = d.blocks[b];
+  j.k = blk.x;
+  j.k2 = blk.y;
+  j.q = blk.z;
+  j.g0x = (blk.w & 3) - 1;
+  j.g0y = ((blk.w >> 2) & 3) - 1;
+  j.g0z = ((blk.w >> 4) & 3) - 1;
+  const long long qb = d.qblk_off[j.q];
+  const long long nblk = d.qblk_off[j.q + 1] - qb;
+  const long long local = b - qb;
+  long long vec = d.qvec_off[j.q] - vbase;
+  if (kind == 0) {
+    j.n0 = j.m0 = 0;
+    j.nn = j.nm = d.nv;
+    vec += local * d.nv * d.nv;
+  } else {
+    j.n0 = j.m0 = d.nv;
+    j.nn = j.nm = d.nc;
+    vec += nblk * d.nv * d.nv + local * d.nc * d.nc;
+  }
+  j.out = out + (size_t)vec * d.ng_max;
+  return j;
+}
+
+template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int ACC>
+__global__ __launch_bounds__(kThreads, 1) void pair_kernel(DevSys d, const float2* __restrict__ u,
+                                                           float2* __restrict__ out, int mode, long long b0,
+                                                           long long vbase) {
+  using C = PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, ACC>;
+  constexpr int M2 = C::M2, M3 = C::M3, LD = C::LD;
+  extern __shared__ float4 sm4[];
+  float2* ub = reinterpret_cast<float2*>(sm4);   // [BMAX][ROWS][LD]
+  float2* S1 = ub + BMAX * ROWS * LD;             // [PMAX][N2][M3]
+  float2* S2 = S1 + PMAX * N2 * M3;               // [PMAX][M2][M3]
+  int2* sg = reinterpret_cast<int2*>(S2 + PMAX * M2 * M3);
+
+  const int tid = threadIdx.x;
+  const Job jb = decode_job(d, mode, b0, vbase, out);
+  const int P = jb.nn * jb.nm;
+  const int NG = d.ngq[jb.q];
+  for (int t = tid; t < NG; t += kThreads) {
+    const char4 g = d.gq[(size_t)jb.q * d.ng_max + t];
+    const int G1 = g.x - jb.g0x, G2 = g.y - jb.g0y, G3 = g.z - jb.g0z;   // G = g_p - G0
+    sg[t] = make_int2(G1, (G2 + F2) * M3 + (G3 + F3));
+  }
+  float2 acc[ACC];
+#pragma unroll
+  for (int a = 0; a < ACC; ++a) acc[a] = make_float2(0.f, 0.f);
+
+  const size_t vol = (size_t)N1 * N2 * N3;
+  const float2* un = u + ((size_t)jb.k * d.nb + jb.n0) * vol;
+  const float2* um = u + ((size_t)jb.k2 * d.nb + jb.m0) * vol;
+  const int nbands = jb.nn + jb.nm;
+
+  for (int j1 = 0; j1 < N1; ++j1) {
+    for (int r0 = 0; r0 < N2; r0 += ROWS) {
+      __syncthreads();
+      for (int idx = tid; idx < nbands * ROWS * N3; idx += kThreads) {
+        const int bi = idx / (ROWS * N3);
+        const int e = idx - bi * (ROWS * N3);
+        const int row = e / N3, j3 = e - row * N3;
+        const float2* src = (bi < jb.nn) ? un + (size_t)bi * vol : um + (size_t)(bi - jb.nn) * vol;
+        ub[(bi * ROWS + row) * LD + j3] = __ldg(src + ((size_t)j1 * N2 + r0 + row) * N3 + j3);
+      }
+      __syncthreads();
+      for (int it = tid; it < P * ROWS; it += kThreads) {      // stage 1: product + z FFT
+        const int p = it / ROWS, row = it - p * ROWS;
+        const int a = p / jb.nm, b = p - a * jb.nm;
+        const float2* xn = ub + (a * ROWS + row) * LD;
+        const float2* xm = ub + ((jb.nn + b) * ROWS + row) * LD;
+        float2 x[N3];
+#pragma unroll
+        for (int j = 0; j < N3; ++j) x[j] = cmul(cconj(xn[j]), xm[j]);
+        fft::line<N3, true>(c_tw, x);
+        float2* dst = S1 + (p * N2 + r0 + row) * M3;
+#pragma unroll
+        for (int f = -F3; f <= F3; ++f) dst[f + F3] = x[(f + N3) % N3];
+      }
+    }
+    __syncthreads();
+    for (int it = tid; it < P * M3; it += kThreads) {          // stage 2: y FFT of kept planes
+      const int p = it / M3, m3 = it - p * M3;
+      float2 y[N2];
+#pragma unroll
+      for (int j = 0; j < N2; ++j) y[j] = S1[(p * N2 + j) * M3 + m3];
+      fft::line<N2, true>(c_tw, y);
+#pragma unroll
+      for (int f = -F2; f <= F2; ++f) S2[(p * M2 + (f + F2)) * M3 + m3] = y[(f + N2) % N2];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < ACC; ++a) {                             // stage 3: x DFT at sphere points
+      const int idx = tid + a * kThreads;
+      if (idx < P * NG) {
+        const int p = idx / NG, t = idx - p * NG;
+        const int2 g = sg[t];
+        const float2 s = S2[p * M2 * M3 + g.y];
+        acc[a] = cadd(acc[a], cmul(s, fft::tw<N1, true>(c_tw, g.x * j1)));
+      }
+    }
+  }
+  const float inv = 1.0f / (float)(N1 * N2 * N3);
+#pragma unroll
+  for (int a = 0; a < ACC; ++a) {
+    const int idx = tid + a * kThreads;
+    if (idx < P * NG) {
+      const int p = idx / NG, t = idx - p * NG;
+      jb.out[(size_t)p * d.ng_max + t] = make_float2(acc[a].x * inv, acc[a].y * inv);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- A6
+__global__ void dipole_kernel(DevSys d, const float2* __restrict__ coef, const double* __restrict__ e,
+                              double gap_floor, double2* __restrict__ P) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= d.dim) return;
+  const int ic = warp % d.nc, iv = (warp / d.nc) % d.nv, k = warp / (d.nv * d.nc);
+  const float2* cv = coef + ((size_t)k * d.nb + iv) * d.npw_max;
+  const float2* cc = coef + ((size_t)k * d.nb + d.nv + ic) * d.npw_max;
+  const double* kg = d.kgq + (size_t)k * d.npw_max;
+  double re = 0.0, im = 0.0;
+  for (int t = lane; t < d.npw[k]; t += 32) {
+    const double2 a = make_double2(cv[t].x, cv[t].y), b = make_double2(cc[t].x, cc[t].y);
+    // conj(a) * b * (qhat.(k+G))
+    re += kg[t] * (a.x * b.x + a.y * b.y);
+    im += kg[t] * (a.x * b.y - a.y * b.x);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) {
+    const double de = fmax(e[(size_t)k * d.nb + d.nv + ic] - e[(size_t)k * d.nb + iv], gap_floor);
+    P[warp] = make_double2(re / de, -im / de);     // conj(sum) / de
+  }
+}
+
+// ---------------------------------------------------------------- dispatch
+typedef void (*RsFn)(DevSys, const float2*, float2*);
+typedef void (*PairFn)(DevSys, const float2*, float2*, int, long long, long long);
+
+struct Variant {
+  int n1, n2, n3, f1, f2, f3, pmax, bmax, ngmax;
+  RsFn rs;
+  size_t rs_smem;
+  PairFn pair;
+  size_t (*pair_smem)(int);
+};
+
+#define BSE_VARIANT(N1, N2, N3, F1, F2, F3, PMAX, BMAX, ROWS, ACC)                                              \
+  Variant {                                                                                                     \
+    N1, N2, N3, F1, F2, F3, PMAX, BMAX, (ACC) * kThreads / (PMAX), realspace_kernel<N1, N2, N3, F1, F2, F3>,    \
+        RsCfg<N1, N2, N3, F1, F2, F3>::smem, pair_kernel<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, ACC>,             \
+        PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, ACC>::smem                                                 \
+  }
+
+const Variant kVariants[] = {
+    BSE_VARIANT(8, 8, 8, 2, 2, 2, 16, 8, 8, 4),
+    BSE_VARIANT(24, 24, 24, 3, 3, 3, 16, 8, 12, 8),
+    BSE_VARIANT(32, 32, 32, 5, 5, 5, 16, 8, 16, 20),
+    BSE_VARIANT(48, 48, 48, 6, 6, 6, 16, 8, 16, 34),
+    BSE_VARIANT(12, 12, 48, 2, 2, 10, 9, 6, 12, 5),
+};
+
+const Variant* pick(const DevSys& d) {
+  const int pmax = (d.nv > d.nc ? d.nv : d.nc);
+  const int pm = (d.nv * d.nc > pmax * pmax) ? d.nv * d.nc : pmax * pmax;
+  for (const Variant& v : kVariants) {
+    if (v.n1 != d.n1 || v.n2 != d.n2 || v.n3 != d.n3) continue;
+    const int f[3] = {v.f1, v.f2, v.f3};
+    bool ok = true;
+    for (int j = 0; j < 3; ++j) ok = ok && d.fwf[j] <= f[j] && d.fpair[j] <= f[j];
+    ok = ok && pm <= v.pmax && d.nb <= v.bmax && (long long)pm * d.ng_max <= (long long)v.ngmax * v.pmax;
+    if (ok) return &v;
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+int upload_twiddles() {
+  float2 h[fft::kTwN];
+  for (int t = 0; t < fft::kTwN; ++t)
+    h[t] = make_float2((float)std::cos(2.0 * kPi * t / fft::kTwN), (float)std::sin(2.0 * kPi * t / fft::kTwN));
+  return (int)cudaMemcpyToSymbol(c_tw, h, sizeof(h));
+}
+
+int pair_supported(const DevSys& d) { return pick(d) != nullptr; }
+
+int launch_realspace(const DevSys& d, const void* coef, void* u, void* stream) {
+  const Variant* v = pick(d);
+  if (!v) return (int)cudaErrorInvalidValue;
+  cudaFuncSetAttribute((const void*)v->rs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->rs_smem);
+  v->rs<<<d.nkpt * d.nb, kThreads, v->rs_smem, (cudaStream_t)stream>>>(d, (const float2*)coef, (float2*)u);
+  return (int)cudaGetLastError();
+}
+
+int launch_pair_exchange(const DevSys& d, const void* u, void* rho_x, void* stream) {
+  const Variant* v = pick(d);
+  if (!v) return (int)cudaErrorInvalidValue;
+  const size_t sm = v->pair_smem(d.ng_max);
+  cudaFuncSetAttribute((const void*)v->pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  v->pair<<<d.nkpt, kThreads, sm, (cudaStream_t)stream>>>(d, (const float2*)u, (float2*)rho_x, 0, 0, 0);
+  return (int)cudaGetLastError();
+}
+
+int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, long long b_begin, long long b_count,
+                       long long vbase, void* stream) {
+  const Variant* v = pick(d);
+  if (!v) return (int)cudaErrorInvalidValue;
+  const size_t sm = v->pair_smem(d.ng_max);
+  cudaFuncSetAttribute((const void*)v->pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  for (long long done = 0; done < b_count;) {
+    const long long chunk = (b_count - done) > (1LL << 29) ? (1LL << 29) : (b_count - done);
+    v->pair<<<(unsigned)(2 * chunk), kThreads, sm, (cudaStream_t)stream>>>(d, (const float2*)u, (float2*)rho_dir, 1,
+                                                                           b_begin + done, vbase);
+    done += chunk;
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_dipole(const DevSys& d, const void* coef, const double* energies, double gap_floor, void* P,
+                  void* stream) {
+  const int threads = 256;
+  const long long blocks = ((long long)d.dim * 32 + threads - 1) / threads;
+  dipole_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(d, (const float2*)coef, energies, gap_floor,
+                                                                       (double2*)P);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace bse

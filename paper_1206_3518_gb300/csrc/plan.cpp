@@ -1,0 +1,553 @@
+// Host planning (step A0) and the C-ABI entry points.
+//
+// Plane-wave spheres |k+G|^2/2 <= Ecut and |q+G|^2/2 <= Ecut (Sec. II C), the
+// Gamma-centred q mesh of k-point differences with the folding vector G0
+// (Sec. III A, q = T q_IBZ + G0 with T = identity), the e-h pair index and the
+// upper (k <= k') block list of the direct term.  Keys are exact: an integer
+// for fcc, a double evaluated in a fixed order for the hexagonal sheet; this
+// file is compiled with -ffp-contract=off so the tables are bit-identical to
+// any other IEEE evaluation of the same expressions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+
+namespace bse {
+
+static thread_local std::string g_last_error = "";
+
+bse_status set_error(bse_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+bse_status cuda_check(int err, const char* what) {
+  if (err == cudaSuccess) return BSE_OK;
+  return set_error(BSE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString((cudaError_t)err));
+}
+
+namespace {
+
+struct Key {
+  double key;
+  int g1, g2, g3;
+  bool operator<(const Key& o) const { return std::tie(key, g1, g2, g3) < std::tie(o.key, o.g1, o.g2, o.g3); }
+};
+
+double cell_volume(const bse_system& s) {
+  if (s.lattice == BSE_LATTICE_FCC) return s.a * s.a * s.a / 4.0;
+  return s.a * s.a * std::sqrt(3.0) / 2.0 * s.c;
+}
+
+void recip_basis(const bse_system& s, double b[3][3]) {
+  const double t = 2.0 * kPi / s.a;
+  if (s.lattice == BSE_LATTICE_FCC) {
+    const double m[3][3] = {{-1, 1, 1}, {1, -1, 1}, {1, 1, -1}};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) b[i][j] = t * m[i][j];
+  } else {
+    b[0][0] = t; b[0][1] = t / std::sqrt(3.0); b[0][2] = 0.0;
+    b[1][0] = 0.0; b[1][1] = 2.0 * t / std::sqrt(3.0); b[1][2] = 0.0;
+    b[2][0] = 0.0; b[2][1] = 0.0; b[2][2] = 2.0 * kPi / s.c;
+  }
+}
+
+int box_bound(const bse_system& s, int j) {
+  double alen = (s.lattice == BSE_LATTICE_FCC) ? s.a / std::sqrt(2.0) : (j < 2 ? s.a : s.c);
+  return (int)(std::sqrt(2.0 * s.ecut) * alen / (2.0 * kPi)) + 2;
+}
+
+// Sorted sphere of mesh offset off = (i1, i2, i3): reduced G with |off/nk + G|^2/2 <= ecut.
+std::vector<int32_t> sphere(const bse_system& s, const int off[3]) {
+  std::vector<Key> keys;
+  const int n = s.nk[0];
+  const int b0 = box_bound(s, 0), b1 = box_bound(s, 1), b2 = box_bound(s, 2);
+  for (int g1 = -b0; g1 <= b0; ++g1)
+    for (int g2 = -b1; g2 <= b1; ++g2)
+      for (int g3 = -b2; g3 <= b2; ++g3) {
+        if (s.lattice == BSE_LATTICE_FCC) {
+          const long long x1 = (long long)n * g1 + off[0], x2 = (long long)n * g2 + off[1],
+                          x3 = (long long)n * g3 + off[2];
+          const long long q = 3 * x1 * x1 + 3 * x2 * x2 + 3 * x3 * x3 - 2 * x1 * x2 - 2 * x1 * x3 - 2 * x2 * x3;
+          const double t = s.a / (2.0 * kPi);
+          const double rhs = 2.0 * s.ecut * (t * t) * (double)(n * n);
+          if ((double)q <= rhs) keys.push_back({(double)q, g1, g2, g3});
+        } else {
+          const long long x1 = (long long)n * g1 + off[0], x2 = (long long)n * g2 + off[1];
+          const double sa = 2.0 * kPi / s.a;
+          const double uc = 2.0 * kPi / s.c;
+          const double c1 = (4.0 / 3.0) * (sa * sa);
+          const double c3 = uc * uc;
+          const double z = (double)(n * g3);
+          const double key = c1 * (double)(x1 * x1 + x1 * x2 + x2 * x2) + c3 * (z * z);
+          if (key <= 2.0 * s.ecut * (double)(n * n)) keys.push_back({key, g1, g2, g3});
+        }
+      }
+  std::sort(keys.begin(), keys.end());
+  std::vector<int32_t> out;
+  out.reserve(keys.size() * 3);
+  for (auto& k : keys) {
+    out.push_back(k.g1);
+    out.push_back(k.g2);
+    out.push_back(k.g3);
+  }
+  return out;
+}
+
+// Grid sizes must divide the 192-entry twiddle table: 2^a 3^b with a <= 6, b <= 1.
+bool is_23_smooth(int n) { return n >= 2 && n <= 64 && 192 % n == 0; }
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
+  bse_system s = in;
+  if (s.lattice != BSE_LATTICE_FCC && s.lattice != BSE_LATTICE_HEX) return set_error(BSE_ERR_ARG, "unknown lattice");
+  if (s.lattice == BSE_LATTICE_FCC && !(s.nk[0] == s.nk[1] && s.nk[1] == s.nk[2]))
+    return set_error(BSE_ERR_ARG, "fcc needs nk1 = nk2 = nk3");
+  if (s.lattice == BSE_LATTICE_HEX && !(s.nk[0] == s.nk[1] && s.nk[2] == 1))
+    return set_error(BSE_ERR_ARG, "hex needs nk1 = nk2 and nk3 = 1");
+  if (s.nk[0] < 1 || s.nv < 1 || s.nc < 1 || s.nv > 4 || s.nc > 4)
+    return set_error(BSE_ERR_ARG, "need nk >= 1 and 1 <= nv, nc <= 4");
+  if (!(s.ecut > 0.0) || !(s.a > 0.0) || (s.lattice == BSE_LATTICE_HEX && !(s.c > 0.0)))
+    return set_error(BSE_ERR_ARG, "ecut, a (and c) must be positive");
+  for (int j = 0; j < 3; ++j)
+    if (!is_23_smooth(s.fft[j])) return set_error(BSE_ERR_ARG, "fft grid sizes must divide 192 (2^a 3^b, b <= 1, <= 64)");
+  if (s.coulomb != BSE_COULOMB_3D && s.coulomb != BSE_COULOMB_SLAB) return set_error(BSE_ERR_ARG, "unknown coulomb");
+  const double qn = std::sqrt(s.qhat[0] * s.qhat[0] + s.qhat[1] * s.qhat[1] + s.qhat[2] * s.qhat[2]);
+  if (!(qn > 0.0)) return set_error(BSE_ERR_ARG, "qhat must be nonzero");
+  for (int j = 0; j < 3; ++j) s.qhat[j] /= qn;
+  sp.sys = s;
+
+  const int nk1 = s.nk[0], nk2 = s.nk[1], nk3 = s.nk[2];
+  const int nkpt = nk1 * nk2 * nk3;
+  DevSys& d = sp.d;
+  d.nkpt = nkpt;
+  d.nq = nkpt;
+  d.nv = s.nv;
+  d.nc = s.nc;
+  d.nb = s.nv + s.nc;
+  d.dim = nkpt * s.nv * s.nc;
+  d.n1 = s.fft[0];
+  d.n2 = s.fft[1];
+  d.n3 = s.fft[2];
+  d.nk1 = nk1;
+  d.nk2 = nk2;
+  d.nk3 = nk3;
+  d.omega_cell = cell_volume(s);
+  d.norm = 1.0 / (d.omega_cell * nkpt);
+  d.prefactor = 8.0 * kPi * d.norm;
+
+  auto offs = [&](int ik, int o[3]) {
+    o[0] = ik / (nk2 * nk3);
+    o[1] = (ik / nk3) % nk2;
+    o[2] = ik % nk3;
+  };
+  sp.gk.resize(nkpt);
+  sp.gq.resize(nkpt);
+  int npw_max = 0, ng_max = 0;
+  for (int j = 0; j < 3; ++j) d.fwf[j] = d.fpair[j] = 0;
+  for (int ik = 0; ik < nkpt; ++ik) {
+    int o[3];
+    offs(ik, o);
+    sp.gk[ik] = sphere(s, o);
+    sp.gq[ik] = sp.gk[ik];          // the q mesh is the k mesh
+    const int n = (int)sp.gk[ik].size() / 3;
+    npw_max = std::max(npw_max, n);
+    ng_max = std::max(ng_max, n);
+    for (int t = 0; t < n; ++t)
+      for (int j = 0; j < 3; ++j) {
+        const int g = sp.gk[ik][3 * t + j];
+        d.fwf[j] = std::max(d.fwf[j], std::abs(g));
+        d.fpair[j] = std::max(d.fpair[j], std::abs(g));
+        if (o[j] != 0) d.fpair[j] = std::max(d.fpair[j], std::abs(g + 1));   // G = g - G0, G0_j = -1
+      }
+  }
+  if (npw_max < d.nb) return set_error(BSE_ERR_ARG, "fewer plane waves than bands");
+  for (int j = 0; j < 3; ++j) {
+    if (s.fft[j] <= 2 * d.fwf[j] + d.fpair[j])
+      return set_error(BSE_ERR_ARG, "fft grid too small for alias-free pair densities (need N > 2 Fwf + Fpair)");
+    if (d.fwf[j] > 120 || d.fpair[j] > 120) return set_error(BSE_ERR_ARG, "sphere too large");
+  }
+  d.npw_max = npw_max;
+  d.ng_max = ng_max;
+  d.ng0 = (int)sp.gq[0].size() / 3;
+
+  // upper blocks grouped by q, then by ik
+  sp.qblk_off.assign(nkpt + 1, 0);
+  sp.qvec_off.assign(nkpt + 1, 0);
+  sp.blocks.clear();
+  const long long per_blk = (long long)s.nv * s.nv + (long long)s.nc * s.nc;
+  for (int iq = 0; iq < nkpt; ++iq) {
+    int qo[3];
+    offs(iq, qo);
+    long long nb = 0;
+    for (int ik = 0; ik < nkpt; ++ik) {
+      int ko[3], k2[3], g0[3];
+      offs(ik, ko);
+      for (int j = 0; j < 3; ++j) {
+        const int n = s.nk[j];
+        const int t = ko[j] + qo[j];
+        k2[j] = t % n;
+        g0[j] = 0;
+        // k' - k = q + G0  with k'_j = (k_j + q_j) mod n  =>  G0_j = -1 when the sum wraps
+        if (t >= n) g0[j] = -1;
+      }
+      const int ik2 = (k2[0] * nk2 + k2[1]) * nk3 + k2[2];
+      if (ik > ik2) continue;
+      sp.blocks.insert(sp.blocks.end(), {ik, ik2, iq, g0[0], g0[1], g0[2]});
+      ++nb;
+    }
+    sp.qblk_off[iq + 1] = sp.qblk_off[iq] + nb;
+    sp.qvec_off[iq + 1] = sp.qvec_off[iq] + nb * per_blk;
+  }
+  d.nblocks = sp.qblk_off[nkpt];
+
+  // ---- device tables (one allocation) ----
+  double b[3][3];
+  recip_basis(s, b);
+  std::vector<char4> h_gk((size_t)nkpt * npw_max, make_char4(0, 0, 0, 0));
+  std::vector<int> h_npw(nkpt), h_ngq(nkpt);
+  std::vector<double> h_kgq((size_t)nkpt * npw_max, 0.0);
+  for (int ik = 0; ik < nkpt; ++ik) {
+    int o[3];
+    offs(ik, o);
+    const int n = (int)sp.gk[ik].size() / 3;
+    h_npw[ik] = h_ngq[ik] = n;
+    for (int t = 0; t < n; ++t) {
+      const int* g = &sp.gk[ik][3 * t];
+      h_gk[(size_t)ik * npw_max + t] = make_char4((signed char)g[0], (signed char)g[1], (signed char)g[2], 0);
+      double kg[3] = {0, 0, 0};
+      for (int i = 0; i < 3; ++i) {
+        const double red = (double)g[i] + (double)o[i] / (double)s.nk[i];
+        for (int j = 0; j < 3; ++j) kg[j] += red * b[i][j];
+      }
+      h_kgq[(size_t)ik * npw_max + t] = s.qhat[0] * kg[0] + s.qhat[1] * kg[1] + s.qhat[2] * kg[2];
+    }
+  }
+  std::vector<int4> h_blocks(d.nblocks);
+  for (long long i = 0; i < d.nblocks; ++i) {
+    const int32_t* r = &sp.blocks[6 * i];
+    const int packed = (r[3] + 1) | ((r[4] + 1) << 2) | ((r[5] + 1) << 4);
+    h_blocks[i] = make_int4(r[0], r[1], r[2], packed);
+  }
+  std::vector<float> h_xs(ng_max, 0.0f);
+  for (int t = 1; t < d.ng0; ++t) {
+    const int* g = &sp.gq[0][3 * t];
+    double p[3] = {0, 0, 0};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) p[j] += (double)g[i] * b[i][j];
+    const double p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+    double v = 4.0 * kPi / p2;
+    if (s.coulomb == BSE_COULOMB_SLAB) {
+      const double zc = 0.5 * s.c;
+      const double ppar = std::sqrt(p[0] * p[0] + p[1] * p[1]);
+      v *= (1.0 - std::exp(-ppar * zc) * std::cos(p[2] * zc));
+    }
+    h_xs[t] = (float)std::sqrt(2.0 * d.norm * v);
+  }
+
+  if (!device) return BSE_OK;
+  size_t off = 0;
+  const size_t o_gk = off; off = align256(off + h_gk.size() * sizeof(char4));
+  const size_t o_npw = off; off = align256(off + h_npw.size() * sizeof(int));
+  const size_t o_ngq = off; off = align256(off + h_ngq.size() * sizeof(int));
+  const size_t o_blk = off; off = align256(off + h_blocks.size() * sizeof(int4));
+  const size_t o_qbo = off; off = align256(off + sp.qblk_off.size() * sizeof(long long));
+  const size_t o_qvo = off; off = align256(off + sp.qvec_off.size() * sizeof(long long));
+  const size_t o_kgq = off; off = align256(off + h_kgq.size() * sizeof(double));
+  const size_t o_xs = off; off = align256(off + h_xs.size() * sizeof(float));
+  char* base = nullptr;
+  bse_status st = cuda_check(cudaMalloc((void**)&base, off), "cudaMalloc(plan tables)");
+  if (st != BSE_OK) return st;
+  sp.dmem = base;
+  auto up = [&](size_t o, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpy(base + o, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+  };
+  int err = up(o_gk, h_gk.data(), h_gk.size() * sizeof(char4));
+  if (!err) err = up(o_npw, h_npw.data(), h_npw.size() * sizeof(int));
+  if (!err) err = up(o_ngq, h_ngq.data(), h_ngq.size() * sizeof(int));
+  if (!err) err = up(o_blk, h_blocks.data(), h_blocks.size() * sizeof(int4));
+  if (!err) err = up(o_qbo, sp.qblk_off.data(), sp.qblk_off.size() * sizeof(long long));
+  if (!err) err = up(o_qvo, sp.qvec_off.data(), sp.qvec_off.size() * sizeof(long long));
+  if (!err) err = up(o_kgq, h_kgq.data(), h_kgq.size() * sizeof(double));
+  if (!err) err = up(o_xs, h_xs.data(), h_xs.size() * sizeof(float));
+  if ((st = cuda_check(err, "cudaMemcpy(plan tables)")) != BSE_OK) return st;
+  d.gk = (const char4*)(base + o_gk);
+  d.npw = (const int*)(base + o_npw);
+  d.gq = d.gk;                        // same spheres (q mesh = k mesh)
+  d.ngq = (const int*)(base + o_ngq);
+  d.blocks = (const int4*)(base + o_blk);
+  d.qblk_off = (const long long*)(base + o_qbo);
+  d.qvec_off = (const long long*)(base + o_qvo);
+  d.kgq = (const double*)(base + o_kgq);
+  d.xscale = (const float*)(base + o_xs);
+  return BSE_OK;
+}
+
+bse_status check_plan(const bse_plan* plan, int s) {
+  if (!plan) return set_error(BSE_ERR_ARG, "plan is NULL");
+  if (s < 0 || s >= (int)plan->sys.size()) return set_error(BSE_ERR_ARG, "system index out of range");
+  return BSE_OK;
+}
+
+bse_status check_device_plan(const bse_plan* plan, int s) {
+  bse_status st = check_plan(plan, s);
+  if (st != BSE_OK) return st;
+  if (!plan->d_status) return set_error(BSE_ERR_ARG, "host-only plan: no device tables");
+  return BSE_OK;
+}
+
+bse_status create(const bse_system* sys, int nsys, bse_plan** out, bool device) {
+  if (!sys || nsys < 1 || !out) return set_error(BSE_ERR_ARG, "need sys, nsys >= 1 and out");
+  *out = nullptr;
+  bse_plan* p = new bse_plan();
+  if (device) cudaGetDevice(&p->device);
+  p->sys.resize(nsys);
+  bse_status st = BSE_OK;
+  for (int i = 0; i < nsys && st == BSE_OK; ++i) st = build_system(sys[i], p->sys[i], device);
+  if (device) {
+    if (st == BSE_OK) st = cuda_check(cudaMalloc((void**)&p->d_status, sizeof(int)), "cudaMalloc(status)");
+    if (st == BSE_OK) st = cuda_check(cudaMemset(p->d_status, 0, sizeof(int)), "cudaMemset(status)");
+    if (st == BSE_OK) st = cuda_check(upload_twiddles(), "twiddle upload");
+  }
+  if (st != BSE_OK) {
+    std::string msg = g_last_error;
+    bse_plan_destroy(p);
+    return set_error(st, msg);
+  }
+  *out = p;
+  return BSE_OK;
+}
+
+}  // namespace
+}  // namespace bse
+
+using namespace bse;
+
+extern "C" {
+
+const char* bse_last_error(void) { return g_last_error.c_str(); }
+
+bse_status bse_plan_create(const bse_system* sys, int nsys, bse_plan** out) { return create(sys, nsys, out, true); }
+
+bse_status bse_plan_create_host(const bse_system* sys, int nsys, bse_plan** out) {
+  return create(sys, nsys, out, false);
+}
+
+bse_status bse_plan_destroy(bse_plan* plan) {
+  if (!plan) return BSE_OK;
+  for (auto& sp : plan->sys)
+    if (sp.dmem) cudaFree(sp.dmem);
+  if (plan->d_status) cudaFree(plan->d_status);
+  delete plan;
+  return BSE_OK;
+}
+
+bse_status bse_plan_info(const bse_plan* plan, int s, bse_info* info) {
+  bse_status st = check_plan(plan, s);
+  if (st != BSE_OK) return st;
+  if (!info) return set_error(BSE_ERR_ARG, "info is NULL");
+  const DevSys& d = plan->sys[s].d;
+  info->nkpt = d.nkpt;
+  info->nb = d.nb;
+  info->dim = d.dim;
+  info->npw_max = d.npw_max;
+  info->ng_max = d.ng_max;
+  info->ng0 = d.ng0;
+  info->nq = d.nq;
+  info->nblocks = d.nblocks;
+  info->omega_cell = d.omega_cell;
+  info->norm = d.norm;
+  info->prefactor = d.prefactor;
+  return BSE_OK;
+}
+
+bse_status bse_gvectors(const bse_plan* plan, int s, int kq, int is_q, int32_t* out, int* n) {
+  bse_status st = check_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const SysPlan& sp = plan->sys[s];
+  if (kq < 0 || kq >= sp.d.nkpt || !n) return set_error(BSE_ERR_ARG, "bad mesh index or n");
+  const auto& v = is_q ? sp.gq[kq] : sp.gk[kq];
+  *n = (int)v.size() / 3;
+  if (out) std::memcpy(out, v.data(), v.size() * sizeof(int32_t));
+  return BSE_OK;
+}
+
+bse_status bse_pair_blocks(const bse_plan* plan, int s, int iq, int32_t* out, int32_t* g0, int* n) {
+  bse_status st = check_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const SysPlan& sp = plan->sys[s];
+  if (iq < 0 || iq >= sp.d.nq || !n) return set_error(BSE_ERR_ARG, "bad q index or n");
+  const long long b0 = sp.qblk_off[iq], b1 = sp.qblk_off[iq + 1];
+  *n = (int)(b1 - b0);
+  for (long long b = b0; b < b1; ++b) {
+    const int32_t* r = &sp.blocks[6 * b];
+    if (out) {
+      out[2 * (b - b0)] = r[0];
+      out[2 * (b - b0) + 1] = r[1];
+    }
+    if (g0)
+      for (int j = 0; j < 3; ++j) g0[3 * (b - b0) + j] = r[3 + j];
+  }
+  return BSE_OK;
+}
+
+bse_status bse_workspace_size(const bse_plan* plan, int s, int kind, long long arg, size_t* bytes) {
+  bse_status st = check_plan(plan, s);
+  if (st != BSE_OK) return st;
+  if (!bytes) return set_error(BSE_ERR_ARG, "bytes is NULL");
+  const DevSys& d = plan->sys[s].d;
+  switch (kind) {
+    case BSE_WS_PAIR:
+      *bytes = (size_t)d.nkpt * d.nb * d.n1 * d.n2 * d.n3 * 8;
+      return BSE_OK;
+    case BSE_WS_KERNEL:
+      if (arg < 1 || arg > d.nq) return set_error(BSE_ERR_ARG, "q chunk out of range");
+      *bytes = kernel_ws_bytes(d, arg);
+      return BSE_OK;
+    case BSE_WS_SPECTRUM:
+      if (arg < 1) return set_error(BSE_ERR_ARG, "nsteps must be >= 1");
+      *bytes = spectrum_ws_bytes(d, arg);
+      return BSE_OK;
+    case BSE_WS_BACKWARD:
+      if (arg < 1) return set_error(BSE_ERR_ARG, "nsteps must be >= 1");
+      *bytes = backward_ws_bytes(d, arg);
+      return BSE_OK;
+  }
+  return set_error(BSE_ERR_ARG, "unknown workspace kind");
+}
+
+bse_status bse_rho_dir_count(const bse_plan* plan, int s, int q_begin, int q_end, long long* nvec) {
+  bse_status st = check_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const SysPlan& sp = plan->sys[s];
+  if (!nvec || q_begin < 0 || q_end > sp.d.nq || q_begin > q_end) return set_error(BSE_ERR_ARG, "bad q range");
+  *nvec = sp.qvec_off[q_end] - sp.qvec_off[q_begin];
+  return BSE_OK;
+}
+
+bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags, const void* coef, const double* energies,
+                              void* rho_x, void* P, void* rho_dir, int q_begin, int q_end, void* ws,
+                              size_t ws_bytes, void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const SysPlan& sp = plan->sys[s];
+  const DevSys& d = sp.d;
+  size_t need = 0;
+  bse_workspace_size(plan, s, BSE_WS_PAIR, 0, &need);
+  if (!ws || ws_bytes < need) return set_error(BSE_ERR_WORKSPACE, "pair workspace too small");
+  if (!pair_supported(d)) return set_error(BSE_ERR_UNSUPPORTED, "no pair-FFT kernel compiled for this grid/sphere");
+  if (flags & BSE_PD_REALSPACE) {
+    if (!coef) return set_error(BSE_ERR_ARG, "coef is NULL");
+    if ((st = cuda_check(launch_realspace(d, coef, ws, stream), "realspace")) != BSE_OK) return st;
+  }
+  if (flags & BSE_PD_EXCHANGE) {
+    if (!rho_x && !P) return set_error(BSE_ERR_ARG, "exchange stage needs rho_x or P");
+    if (rho_x && (st = cuda_check(launch_pair_exchange(d, ws, rho_x, stream), "pair exchange")) != BSE_OK) return st;
+    if (P) {
+      if (!coef || !energies) return set_error(BSE_ERR_ARG, "dipole needs coef and energies");
+      if ((st = cuda_check(launch_dipole(d, coef, energies, sp.sys.gap_floor, P, stream), "dipole")) != BSE_OK)
+        return st;
+    }
+  }
+  if (flags & BSE_PD_DIRECT) {
+    if (!rho_dir || q_begin < 0 || q_end > d.nq || q_begin >= q_end) return set_error(BSE_ERR_ARG, "bad direct range");
+    const long long b0 = sp.qblk_off[q_begin], nb = sp.qblk_off[q_end] - b0, vb = sp.qvec_off[q_begin];
+    if ((st = cuda_check(launch_pair_direct(d, ws, rho_dir, b0, nb, vb, stream), "pair direct")) != BSE_OK)
+      return st;
+  }
+  return BSE_OK;
+}
+
+bse_status bse_build_kernel(bse_plan* plan, int s, unsigned flags, const void* rho_x, const void* rho_dir,
+                            int q_begin, int q_end, const void* W, const double* energies, double delta, int prec,
+                            void* H, void* ws, size_t ws_bytes, void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const DevSys& d = plan->sys[s].d;
+  if (!H) return set_error(BSE_ERR_ARG, "H is NULL");
+  if (prec != BSE_PREC_FP32 && prec != BSE_PREC_BF16X3) return set_error(BSE_ERR_ARG, "unknown precision");
+  if (flags & BSE_BK_INIT) {
+    if (!rho_x || !energies) return set_error(BSE_ERR_ARG, "init needs rho_x and energies");
+    if ((st = cuda_check(launch_kernel_init(d, rho_x, energies, delta, H, stream), "kernel init")) != BSE_OK)
+      return st;
+  }
+  if (flags & BSE_BK_DIRECT) {
+    if (!rho_dir || !W || q_begin < 0 || q_end > d.nq || q_begin >= q_end)
+      return set_error(BSE_ERR_ARG, "direct stage needs rho_dir, W and a q range");
+    if (!ws || ws_bytes < kernel_ws_bytes(d, q_end - q_begin))
+      return set_error(BSE_ERR_WORKSPACE, "kernel workspace too small");
+    const SysPlan& sp = plan->sys[s];
+    const long long b0 = sp.qblk_off[q_begin], nb = sp.qblk_off[q_end] - b0, vb = sp.qvec_off[q_begin];
+    const long long w = (d.nc * d.nc < d.nv * d.nv) ? d.nc * d.nc : d.nv * d.nv;
+    long long max_rows = 0;
+    for (int q = q_begin; q < q_end; ++q) max_rows = std::max(max_rows, (sp.qblk_off[q + 1] - sp.qblk_off[q]) * w);
+    const int e = launch_kernel_direct_range(d, rho_dir, q_begin, q_end, b0, nb, vb, max_rows, W, prec, H, ws, stream);
+    if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "precision not available in this build");
+    if ((st = cuda_check(e, "kernel direct")) != BSE_OK) return st;
+  }
+  return BSE_OK;
+}
+
+bse_status bse_apply_H(bse_plan* plan, int s, const void* H, const void* X, void* Y, int nvec, void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  if (!H || !X || !Y || nvec < 1) return set_error(BSE_ERR_ARG, "apply_H needs H, X, Y and nvec >= 1");
+  return cuda_check(launch_apply_h(plan->sys[s].d, H, X, Y, nvec, stream), "apply_H");
+}
+
+bse_status bse_spectrum(bse_plan* plan, int s, const void* H, const void* P, int nsteps, const double* omega, int nw,
+                        double eta, double* eps2, double* ab, int* steps_done, void* ws, size_t ws_bytes,
+                        void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const DevSys& d = plan->sys[s].d;
+  if (!H || !P || !omega || !eps2 || !ab || !steps_done || nsteps < 1 || nw < 0 || !(eta > 0.0))
+    return set_error(BSE_ERR_ARG, "spectrum needs H, P, omega, eps2, ab, steps_done, nsteps >= 1, eta > 0");
+  if (nsteps > d.dim) return set_error(BSE_ERR_ARG, "nsteps > dim");
+  if (!ws || ws_bytes < spectrum_ws_bytes(d, nsteps)) return set_error(BSE_ERR_WORKSPACE, "spectrum workspace too small");
+  const int e = launch_spectrum(d, H, P, nsteps, omega, nw, eta, eps2, ab, steps_done, ws, plan->d_status, stream);
+  if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "cooperative launch not possible on this device");
+  return cuda_check(e, "spectrum");
+}
+
+bse_status bse_spectrum_backward(bse_plan* plan, int s, const void* H, const void* P, int nsteps,
+                                 const double* omega, int nw, double eta, const double* dL_deps2,
+                                 const void* rho_x, const void* rho_dir, const void* W, double* dL_ddelta,
+                                 void* dL_dH, void* dL_drho_x, void* dL_drho_dir, void* dL_dW, void* ws,
+                                 size_t ws_bytes, void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const DevSys& d = plan->sys[s].d;
+  if (!H || !P || !omega || !dL_deps2 || !dL_ddelta || nsteps < 1 || nw < 1 || !(eta > 0.0))
+    return set_error(BSE_ERR_ARG, "backward needs H, P, omega, dL_deps2, dL_ddelta, nsteps >= 1, eta > 0");
+  if (nsteps > d.dim) return set_error(BSE_ERR_ARG, "nsteps > dim");
+  if ((dL_drho_x && !rho_x) || ((dL_drho_dir || dL_dW) && (!rho_dir || !W)) || (dL_drho_x && !W && false))
+    return set_error(BSE_ERR_ARG, "chained gradients need their forward inputs");
+  if (!ws || ws_bytes < backward_ws_bytes(d, nsteps)) return set_error(BSE_ERR_WORKSPACE, "backward workspace too small");
+  const int e = launch_backward(d, H, P, nsteps, omega, nw, eta, dL_deps2, rho_x, rho_dir, W, dL_ddelta, dL_dH,
+                                dL_drho_x, dL_drho_dir, dL_dW, ws, plan->d_status, stream);
+  if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "cooperative launch not possible on this device");
+  return cuda_check(e, "spectrum backward");
+}
+
+bse_status bse_status_read(bse_plan* plan, void* stream) {
+  if (!plan || !plan->d_status) return set_error(BSE_ERR_ARG, "plan is NULL or host-only");
+  bse_status st = cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
+  if (st != BSE_OK) return st;
+  int h = 0;
+  if ((st = cuda_check(cudaMemcpy(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read")) != BSE_OK)
+    return st;
+  cudaMemset(plan->d_status, 0, sizeof(int));
+  if (h != 0) return set_error((bse_status)h, "device-side status set by a kernel");
+  return BSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+"""Chaining of the C-ABI calls into one forward pass of the hot path (A1-A8).
+
+Only buffer allocation (torch) and call order live here; every step runs in
+the CUDA library.  ``Forward`` preallocates every buffer for one system so a
+timed loop allocates nothing.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import bse
+
+
+class Forward:
+    """Buffers and call sequence for one system of a plan.
+
+    qchunk: q points per pair-density/direct-term chunk (rho_dir is streamed);
+    keep_rho_dir: keep the direct pair densities of every q (needed by the adjoint).
+    """
+
+    def __init__(self, plan: bse.Plan, s: int = 0, nsteps: int = 100, nw: int = 1000, qchunk: int | None = None,
+                 keep_rho_dir: bool = False, device="cuda"):
+        self.plan, self.s = plan, s
+        inf = plan.info(s)
+        self.info = inf
+        self.dim, self.nq, self.ng_max = inf["dim"], inf["nq"], inf["ng_max"]
+        self.nsteps = nsteps
+        if keep_rho_dir or qchunk is None:
+            qchunk = self.nq
+        self.qchunk = qchunk
+        dev = torch.device(device)
+        c64, c128 = torch.complex64, torch.complex128
+        self.ws_pair = torch.empty(bse.bse_workspace_size(plan, s, bse.BSE_WS_PAIR) // 8, dtype=c64, device=dev)
+        self.ws_kernel = torch.empty(max(1, bse.bse_workspace_size(plan, s, bse.BSE_WS_KERNEL, qchunk) // 8),
+                                     dtype=c64, device=dev)
+        self.ws_spec = torch.empty(bse.bse_workspace_size(plan, s, bse.BSE_WS_SPECTRUM, nsteps) // 8 + 1,
+                                   dtype=c64, device=dev)
+        self.rho_x = torch.zeros(self.dim, self.ng_max, dtype=c64, device=dev)
+        self.P = torch.zeros(self.dim, dtype=c128, device=dev)
+        self.chunks = [(q, min(q + qchunk, self.nq)) for q in range(0, self.nq, qchunk)]
+        nvec = max(bse.bse_rho_dir_count(plan, s, a, b) for a, b in self.chunks)
+        self.rho_dir = torch.zeros(nvec, self.ng_max, dtype=c64, device=dev)
+        self.H = torch.empty(self.dim, self.dim, dtype=c64, device=dev)
+        self.eps2 = torch.zeros(nw, dtype=torch.float64, device=dev)
+        self.ab = torch.zeros(2 * nsteps, dtype=torch.float64, device=dev)
+        self.steps_done = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def build(self, coef, energies, W, delta, prec=bse.BSE_PREC_FP32):
+        """A1-A6: pair densities, dipole and H (direct term streamed over q chunks)."""
+        p, s = self.plan, self.s
+        bse.bse_pair_densities(p, s, bse.BSE_PD_REALSPACE | bse.BSE_PD_EXCHANGE, coef, energies, self.rho_x, self.P,
+                               None, 0, 0, self.ws_pair)
+        bse.bse_build_kernel(p, s, bse.BSE_BK_INIT, self.rho_x, None, 0, 0, None, energies, delta, prec, self.H,
+                             None)
+        for q0, q1 in self.chunks:
+            bse.bse_pair_densities(p, s, bse.BSE_PD_DIRECT, None, None, None, None, self.rho_dir, q0, q1, self.ws_pair)
+            bse.bse_build_kernel(p, s, bse.BSE_BK_DIRECT, None, self.rho_dir, q0, q1, W, None, delta, prec, self.H,
+                                 self.ws_kernel)
+        return self.H
+
+    def spectrum(self, omega, eta, nsteps=None):
+        """A7-A8 on the current H and P."""
+        n = self.nsteps if nsteps is None else nsteps
+        bse.bse_spectrum(self.plan, self.s, self.H, self.P, n, omega, eta, self.eps2[: omega.numel()], self.ab,
+                         self.steps_done, self.ws_spec)
+        return self.eps2[: omega.numel()]

@@ -1,0 +1,88 @@
+"""Host logic of the C ABI (no GPU): symbol exports, bit-exact A0 tables against the oracle."""
+import re
+
+import numpy as np
+import pytest
+
+from oracle import geometry as geo
+from oracle import kernel as ok
+from oracle import spectrum as osp
+from synth import SystemSpec, config_spec, slab_batch_specs
+
+
+@pytest.fixture(scope="module")
+def bse():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1206_3518_gb300 import bse as b
+    b.load()
+    return b
+
+
+def test_library_exports_every_declared_symbol(bse):
+    import os
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "bse.h")).read()
+    declared = set(re.findall(r"^(?:bse_status|const char\*)\s+(bse_\w+)\s*\(", hdr, re.M))
+    assert len(declared) >= 14
+    lib = bse.load()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared <= set(bse.EXPORTED)
+
+
+@pytest.mark.parametrize("spec", [config_spec("fcc_4x4x4_3v3c"), slab_batch_specs(0)[1],
+                                  SystemSpec("fcc_tiny", "fcc", 10.0, 0.0, (2, 2, 2), 2, 2, 1.0, (8, 8, 8), "3d")])
+def test_spheres_bit_exact_against_oracle(bse, spec):
+    plan = bse.Plan([spec], host_only=True)
+    kr = geo.mesh_offsets(spec)
+    step = max(1, spec.nkpt // 40)
+    for ik in range(0, spec.nkpt, step):
+        g = bse.bse_gvectors(plan, 0, ik, 0)
+        assert np.array_equal(g, geo.sphere(spec, tuple(kr[ik])))
+        assert np.array_equal(bse.bse_gvectors(plan, 0, ik, 1), g)
+
+
+def test_blocks_and_folds_bit_exact_against_oracle(bse, cfg1):
+    spec = cfg1.spec
+    plan = bse.Plan([spec], host_only=True)
+    kr = geo.mesh_offsets(spec)
+    seen = set()
+    for iq in range(spec.nkpt):
+        blk, g0 = bse.bse_pair_blocks(plan, 0, iq)
+        assert np.all(np.diff(blk[:, 0]) > 0)                     # ascending k within a q
+        for (ik, ik2), g in zip(blk, g0):
+            assert ik <= ik2
+            q, _, og0 = geo.fold(spec, kr[ik], kr[ik2])
+            assert q == iq and np.array_equal(og0, g)
+            seen.add((int(ik), int(ik2)))
+    assert seen == set(geo.upper_blocks(spec))
+
+
+def test_info_constants_match_oracle(bse, cfg1):
+    spec = cfg1.spec
+    inf = bse.Plan([spec], host_only=True).info(0)
+    assert inf["dim"] == 576 and inf["nblocks"] == 2080 and inf["ng0"] == 113
+    assert inf["norm"] == ok.norm_factor(spec)
+    assert abs(inf["prefactor"] - osp.prefactor(spec)) <= 1e-18
+    assert bse.bse_rho_dir_count(bse.Plan([spec], host_only=True), 0, 0, 64) == 2080 * (9 + 9)
+
+
+@pytest.mark.parametrize("bad, msg", [
+    (dict(fft=(9, 9, 9)), "divide 192"),
+    (dict(fft=(8, 8, 8)), "alias-free"),
+    (dict(nk=(4, 4, 2)), "nk1 = nk2 = nk3"),
+    (dict(nv=5), "nv, nc"),
+])
+def test_invalid_systems_rejected(bse, bad, msg):
+    spec = config_spec("fcc_4x4x4_3v3c").replace(**bad)
+    with pytest.raises(bse.BseError) as e:
+        bse.Plan([spec], host_only=True)
+    assert e.value.code == bse.BSE_ERR_ARG and msg in str(e.value)
+
+
+def test_host_only_plan_refuses_compute(bse, cfg1):
+    plan = bse.Plan([cfg1.spec], host_only=True)
+    with pytest.raises(bse.BseError) as e:
+        bse.load().bse_apply_H(plan.handle, 0, None, None, None, 1, None)
+        bse._check(bse.load().bse_apply_H(plan.handle, 0, None, None, None, 1, None))
+    assert e.value.code == bse.BSE_ERR_ARG
