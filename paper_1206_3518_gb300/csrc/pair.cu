@@ -311,7 +311,7 @@ const Variant* pick(const DevSys& d) {
     const int f[3] = {v.f1, v.f2, v.f3};
     bool ok = true;
     for (int j = 0; j < 3; ++j) ok = ok && d.fwf[j] <= f[j] && d.fpair[j] <= f[j];
-    ok = ok && pm <= v.pmax && d.nb <= v.bmax && (long long)pm * d.ng_max <= (long long)v.ngmax * v.pmax;
+    ok = ok && pm <= v.pmax && d.nb <= v.bmax && 2 * pmax <= v.bmax && (long long)pm * d.ng_max <= (long long)v.ngmax * v.pmax;
     if (ok) return &v;
   }
   return nullptr;
