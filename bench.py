@@ -224,6 +224,52 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_stage(args):
+    """One stage alone on the bench workload (for ncu captures); prints per-launch CUDA-event times."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1206_3518_gb300 import bse
+    from paper_1206_3518_gb300.pipeline import Forward
+
+    spec, s = make_inputs(args.config)
+    plan = bse.Plan([spec])
+    qchunk = args.qchunk or (16 if args.only == "pair" else None)
+    F = Forward(plan, 0, nsteps=spec.nsteps, nw=spec.nw, qchunk=qchunk)
+    dev = torch.device("cuda")
+    coef = torch.as_tensor(s.coef.astype(np.complex64), device=dev)
+    en = torch.as_tensor(s.energies, device=dev)
+    om = torch.as_tensor(s.omega, device=dev)
+    if args.only == "spectrum":
+        W = torch.as_tensor(s.W, device=dev)
+        F.build(coef, en, W, spec.delta)
+    bse.bse_pair_densities(plan, 0, bse.BSE_PD_REALSPACE | bse.BSE_PD_EXCHANGE, coef, en, F.rho_x, F.P, None, 0, 0,
+                           F.ws_pair)
+    q0, q1 = F.chunks[min(1, len(F.chunks) - 1)]
+
+    def once():
+        if args.only == "pair":
+            bse.bse_pair_densities(plan, 0, bse.BSE_PD_DIRECT, None, None, None, None, F.rho_dir, q0, q1, F.ws_pair)
+        else:
+            F.spectrum(om, spec.eta)
+
+    for _ in range(args.warmup):
+        once()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        once()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    bse.bse_status_read(plan)
+    nblk = sum(len(bse.bse_pair_blocks(plan, 0, q)[0]) for q in range(q0, q1)) if args.only == "pair" else 0
+    print(json.dumps({"stage": args.only, "config": spec.name, "ms": times, "q_range": [q0, q1], "blocks": nblk}))
+
+
 def roofline(stage, ms, spec, inf, peaks, src, nchunks):
     """Algorithmic work of the dominant stage per launch over its measured mean duration."""
     dim = inf["dim"]
@@ -323,9 +369,15 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default="all", choices=["all", "pair", "spectrum"],
+                    help="profiling aid: run one stage (pair: realspace + a q chunk of pair densities; "
+                         "spectrum: Haydock on an H built once before the loop)")
+    ap.add_argument("--qchunk", type=int, default=0, help="q points per direct-term chunk (0 = all)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only != "all":
+        run_stage(args)
     else:
         run_ours(args)
 

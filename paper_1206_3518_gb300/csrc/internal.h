@@ -26,6 +26,7 @@ struct DevSys {
   const int4* blocks;             // [nblocks] (ik, ik2, iq, g0 packed as (g0+1) bits)
   const long long* qblk_off;      // [nq+1] first block of each q (blocks sorted by q, then ik)
   const long long* qvec_off;      // [nq+1] first rho_dir vector of each q
+  const int* blkidx;              // [nq][nkpt] global block of (q, k) with k <= k + q, else -1
   const double* kgq;              // [nkpt][npw_max] qhat.(k+G), Cartesian
   const float* xscale;            // [ng_max] sqrt(2 vbar(G) / (Omega Nk)), 0 at G = 0 and beyond ng0
   long long nblocks;
@@ -55,8 +56,8 @@ bse_status cuda_check(int err, const char* what);
 // Kernel launchers (defined in the .cu files); all return cudaError_t as int.
 int launch_realspace(const DevSys& d, const void* coef, void* u, void* stream);
 int launch_pair_exchange(const DevSys& d, const void* u, void* rho_x, void* stream);
-int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, long long b_begin, long long b_count,
-                       long long vbase, void* stream);
+int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, int q_begin, int q_end, long long vbase,
+                       void* stream);
 int launch_dipole(const DevSys& d, const void* coef, const double* energies, double gap_floor, void* P, void* stream);
 int pair_supported(const DevSys& d);
 

@@ -105,38 +105,63 @@ __global__ __launch_bounds__(kThreads) void realspace_kernel(DevSys d, const flo
 }
 
 // ---------------------------------------------------------------- A2
-template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int ACC>
+// Template parameters: grid N1 x N2 x N3; kept windows |f2| <= F2, |f3| <= F3; PMAX band
+// products and BMAX band slabs per CTA; ROWS z-lines per pipelined chunk; ACC sphere
+// accumulators per thread; THREADS per CTA; MERGED = one CTA computes both the vv' and
+// the cc' products of a block (else one CTA per block and group).
+template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int ACC, int THREADS, bool MERGED>
 struct PairCfg {
   static constexpr int M2 = 2 * F2 + 1, M3 = 2 * F3 + 1;
-  static constexpr int LD = N3 + 1;    // padded z-line stride in shared memory (conflict-free)
+  static constexpr int LD = N3 + 2;    // z-line stride in shared memory: 16-B aligned rows, float4 reads conflict-free
+  static constexpr int NCH = N1 * (N2 / ROWS);
+  static_assert(N2 % ROWS == 0, "ROWS must divide N2");
   static size_t smem(int ng_max) {
-    return sizeof(float2) * ((size_t)BMAX * ROWS * LD + (size_t)PMAX * N2 * M3 + (size_t)PMAX * M2 * M3) +
+    return sizeof(float2) * ((size_t)2 * BMAX * ROWS * LD + (size_t)PMAX * N2 * M3 + (size_t)PMAX * M2 * M3) +
            sizeof(int2) * (size_t)ng_max;
   }
 };
 
+// Jobs are laid out over the (q, k) cells of a q chunk in tiles of kTQ x kTK so that
+// CTAs running together share wavefunction slabs in L2.
+constexpr int kTQ = 8, kTK = 16;
+
 struct Job {
-  int k, k2, n0, nn, m0, nm, q, g0x, g0y, g0z;
-  float2* out;
+  int k, k2, a0, na, b0, nb, q, g0x, g0y, g0z;
+  int mode;             // 0 exchange (v x c), 1 vv', 2 cc', 3 vv' then cc'
+  float2* out_v;        // first output vector of the vv' (or exchange) products
+  float2* out_c;        // first output vector of the cc' products
 };
 
-// mode 0: exchange set (one job per k: v x c at k = k', q = 0);
-// mode 1: direct set (two jobs per upper block: v x v' and c x c' on the sphere of fold(k'-k)).
-__device__ __forceinline__ Job decode_job(const DevSys& d, int mode, long long b0, long long vbase, float2* out) {
-  Job j;
+__device__ __forceinline__ bool decode_job(const DevSys& d, int mode, bool merged, int q0, int nqc, long long vbase,
+                                           float2* out, Job& j) {
   if (mode == 0) {
     j.k = j.k2 = blockIdx.x;
-    j.n0 = 0;
-    j.nn = d.nv;
-    j.m0 = d.nv;
-    j.nm = d.nc;
+    j.a0 = 0;
+    j.na = d.nv;
+    j.b0 = d.nv;
+    j.nb = d.nc;
     j.q = 0;
     j.g0x = j.g0y = j.g0z = 0;
-    j.out = out + (size_t)blockIdx.x * d.nv * d.nc * d.ng_max;
-    return j;
+    j.mode = 0;
+    j.out_v = out + (size_t)blockIdx.x * d.nv * d.nc * d.ng_max;
+    j.out_c = nullptr;
+    return true;
   }
-  const long long b = b0 + (blockIdx.x >> 1);
-  const int kind = blockIdx.x & 1;
+  long long cell = blockIdx.x;
+  int group = 0;
+  if (!merged) {
+    group = (int)(cell & 1);
+    cell >>= 1;
+  }
+  const int ntk = (d.nkpt + kTK - 1) / kTK;
+  const long long tile = cell / (kTQ * kTK);
+  const int u = (int)(cell - tile * (kTQ * kTK));
+  const int tq = (int)(tile / ntk), tk = (int)(tile - (long long)tq * ntk);
+  const int q = q0 + tq * kTQ + u / kTK;
+  const int k = tk * kTK + u % kTK;
+  if (q >= q0 + nqc || k >= d.nkpt) return false;
+  const int b = d.blkidx[(size_t)q * d.nkpt + k];
+  if (b < 0) return false;
   const int4 blk = d.blocks[b];
   j.k = blk.x;
   j.k2 = blk.y;
@@ -144,40 +169,84 @@ __device__ __forceinline__ Job decode_job(const DevSys& d, int mode, long long b
   j.g0x = (blk.w & 3) - 1;
   j.g0y = ((blk.w >> 2) & 3) - 1;
   j.g0z = ((blk.w >> 4) & 3) - 1;
-  const long long qb = d.qblk_off[j.q];
-  const long long nblk = d.qblk_off[j.q + 1] - qb;
+  const long long qb = d.qblk_off[q];
+  const long long nblk = d.qblk_off[q + 1] - qb;
   const long long local = b - qb;
-  long long vec = d.qvec_off[j.q] - vbase;
-  if (kind == 0) {
-    j.n0 = j.m0 = 0;
-    j.nn = j.nm = d.nv;
-    vec += local * d.nv * d.nv;
+  const long long base = d.qvec_off[q] - vbase;
+  j.out_v = out + (size_t)(base + local * d.nv * d.nv) * d.ng_max;
+  j.out_c = out + (size_t)(base + nblk * d.nv * d.nv + local * d.nc * d.nc) * d.ng_max;
+  if (merged) {
+    j.mode = 3;
+    j.a0 = j.b0 = 0;
+    j.na = j.nb = d.nb;
+  } else if (group == 0) {
+    j.mode = 1;
+    j.a0 = j.b0 = 0;
+    j.na = j.nb = d.nv;
   } else {
-    j.n0 = j.m0 = d.nv;
-    j.nn = j.nm = d.nc;
-    vec += nblk * d.nv * d.nv + local * d.nc * d.nc;
+    j.mode = 2;
+    j.a0 = j.b0 = d.nv;
+    j.na = j.nb = d.nc;
   }
-  j.out = out + (size_t)vec * d.ng_max;
-  return j;
+  return true;
 }
 
-template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int ACC>
-__global__ __launch_bounds__(kThreads, 1) void pair_kernel(DevSys d, const float2* __restrict__ u,
-                                                           float2* __restrict__ out, int mode, long long b0,
-                                                           long long vbase) {
-  using C = PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, ACC>;
-  constexpr int M2 = C::M2, M3 = C::M3, LD = C::LD;
+// product p -> (slab of the n band, slab of the m band, output vector)
+__device__ __forceinline__ void product_of(const DevSys& d, const Job& j, int p, int& sa, int& sb, float2*& dst) {
+  const int nv = d.nv, nc = d.nc;
+  if (j.mode == 0) {                       // (v, c) at k = k'
+    sa = p / nc;
+    sb = j.na + p % nc;
+    dst = j.out_v + (size_t)p * d.ng_max;
+  } else if (j.mode == 1) {                // (v, v')
+    sa = p / nv;
+    sb = j.na + p % nv;
+    dst = j.out_v + (size_t)p * d.ng_max;
+  } else if (j.mode == 2) {                // (c, c')
+    sa = p / nc;
+    sb = j.na + p % nc;
+    dst = j.out_c + (size_t)p * d.ng_max;
+  } else if (p < nv * nv) {                // merged: (v, v') then (c, c'); slabs hold all nb bands
+    sa = p / nv;
+    sb = j.na + p % nv;
+    dst = j.out_v + (size_t)p * d.ng_max;
+  } else {
+    const int t = p - nv * nv;
+    sa = nv + t / nc;
+    sb = j.na + nv + t % nc;
+    dst = j.out_c + (size_t)t * d.ng_max;
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int ACC, int THREADS, bool MERGED>
+__global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2* __restrict__ u,
+                                                          float2* __restrict__ out, int mode, int q0, int nqc,
+                                                          long long vbase) {
+  using C = PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, ACC, THREADS, MERGED>;
+  constexpr int M2 = C::M2, M3 = C::M3, LD = C::LD, NCH = C::NCH;
+  constexpr int CPR = N2 / ROWS;            // chunks per slab
   extern __shared__ float4 sm4[];
-  float2* ub = reinterpret_cast<float2*>(sm4);   // [BMAX][ROWS][LD]
-  float2* S1 = ub + BMAX * ROWS * LD;             // [PMAX][N2][M3]
+  float2* ub = reinterpret_cast<float2*>(sm4);   // [2][BMAX][ROWS][LD]
+  float2* S1 = ub + 2 * BMAX * ROWS * LD;         // [PMAX][N2][M3]
   float2* S2 = S1 + PMAX * N2 * M3;               // [PMAX][M2][M3]
   int2* sg = reinterpret_cast<int2*>(S2 + PMAX * M2 * M3);
 
+  Job jb;
+  if (!decode_job(d, mode, MERGED, q0, nqc, vbase, out, jb)) return;
   const int tid = threadIdx.x;
-  const Job jb = decode_job(d, mode, b0, vbase, out);
-  const int P = jb.nn * jb.nm;
+  const int P = (jb.mode == 0) ? d.nv * d.nc
+              : (jb.mode == 1) ? d.nv * d.nv
+              : (jb.mode == 2) ? d.nc * d.nc : d.nv * d.nv + d.nc * d.nc;
   const int NG = d.ngq[jb.q];
-  for (int t = tid; t < NG; t += kThreads) {
+  for (int t = tid; t < NG; t += THREADS) {
     const char4 g = d.gq[(size_t)jb.q * d.ng_max + t];
     const int G1 = g.x - jb.g0x, G2 = g.y - jb.g0y, G3 = g.z - jb.g0z;   // G = g_p - G0
     sg[t] = make_int2(G1, (G2 + F2) * M3 + (G3 + F3));
@@ -187,64 +256,89 @@ __global__ __launch_bounds__(kThreads, 1) void pair_kernel(DevSys d, const float
   for (int a = 0; a < ACC; ++a) acc[a] = make_float2(0.f, 0.f);
 
   const size_t vol = (size_t)N1 * N2 * N3;
-  const float2* un = u + ((size_t)jb.k * d.nb + jb.n0) * vol;
-  const float2* um = u + ((size_t)jb.k2 * d.nb + jb.m0) * vol;
-  const int nbands = jb.nn + jb.nm;
+  const float2* ua = u + ((size_t)jb.k * d.nb + jb.a0) * vol;
+  const float2* ubb = u + ((size_t)jb.k2 * d.nb + jb.b0) * vol;
+  const int nbands = jb.na + jb.nb;
 
-  for (int j1 = 0; j1 < N1; ++j1) {
-    for (int r0 = 0; r0 < N2; r0 += ROWS) {
+  auto issue = [&](int c) {
+    const int j1 = c / CPR, r0 = (c - j1 * CPR) * ROWS;
+    float2* dstb = ub + (size_t)(c & 1) * BMAX * ROWS * LD;
+    constexpr int H = N3 / 2;               // 16-byte pieces per z-line
+    for (int idx = tid; idx < nbands * ROWS * H; idx += THREADS) {
+      const int bi = idx / (ROWS * H);
+      const int rem = idx - bi * (ROWS * H);
+      const int row = rem / H, h = rem - row * H;
+      const float2* src = (bi < jb.na) ? ua + (size_t)bi * vol : ubb + (size_t)(bi - jb.na) * vol;
+      cp_async16(dstb + ((size_t)bi * ROWS + row) * LD + 2 * h, src + ((size_t)j1 * N2 + r0 + row) * N3 + 2 * h);
+    }
+    cp_async_commit();
+  };
+
+  issue(0);
+  for (int c = 0; c < NCH; ++c) {
+    if (c + 1 < NCH) {
+      issue(c + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const int j1 = c / CPR, r0 = (c - j1 * CPR) * ROWS;
+    const float2* buf = ub + (size_t)(c & 1) * BMAX * ROWS * LD;
+    for (int it = tid; it < P * ROWS; it += THREADS) {          // stage 1: product + z FFT
+      const int p = it / ROWS, row = it - p * ROWS;
+      int sa, sb;
+      float2* dst_unused;
+      product_of(d, jb, p, sa, sb, dst_unused);
+      const float4* xa = reinterpret_cast<const float4*>(buf + ((size_t)sa * ROWS + row) * LD);
+      const float4* xb = reinterpret_cast<const float4*>(buf + ((size_t)sb * ROWS + row) * LD);
+      float2 x[N3];
+#pragma unroll
+      for (int h = 0; h < N3 / 2; ++h) {
+        const float4 va = xa[h], vb = xb[h];
+        x[2 * h] = make_float2(va.x * vb.x + va.y * vb.y, va.x * vb.y - va.y * vb.x);          // conj(a) b
+        x[2 * h + 1] = make_float2(va.z * vb.z + va.w * vb.w, va.z * vb.w - va.w * vb.z);
+      }
+      fft::line<N3, true>(c_tw, x);
+      float2* s1 = S1 + ((size_t)p * N2 + r0 + row) * M3;
+#pragma unroll
+      for (int f = -F3; f <= F3; ++f) s1[f + F3] = x[(f + N3) % N3];
+    }
+    if (r0 + ROWS == N2) {                                       // slab complete
       __syncthreads();
-      for (int idx = tid; idx < nbands * ROWS * N3; idx += kThreads) {
-        const int bi = idx / (ROWS * N3);
-        const int e = idx - bi * (ROWS * N3);
-        const int row = e / N3, j3 = e - row * N3;
-        const float2* src = (bi < jb.nn) ? un + (size_t)bi * vol : um + (size_t)(bi - jb.nn) * vol;
-        ub[(bi * ROWS + row) * LD + j3] = __ldg(src + ((size_t)j1 * N2 + r0 + row) * N3 + j3);
+      for (int it = tid; it < P * M3; it += THREADS) {          // stage 2: y FFT of kept planes
+        const int p = it / M3, m3 = it - p * M3;
+        float2 y[N2];
+#pragma unroll
+        for (int j = 0; j < N2; ++j) y[j] = S1[((size_t)p * N2 + j) * M3 + m3];
+        fft::line<N2, true>(c_tw, y);
+#pragma unroll
+        for (int f = -F2; f <= F2; ++f) S2[((size_t)p * M2 + (f + F2)) * M3 + m3] = y[(f + N2) % N2];
       }
       __syncthreads();
-      for (int it = tid; it < P * ROWS; it += kThreads) {      // stage 1: product + z FFT
-        const int p = it / ROWS, row = it - p * ROWS;
-        const int a = p / jb.nm, b = p - a * jb.nm;
-        const float2* xn = ub + (a * ROWS + row) * LD;
-        const float2* xm = ub + ((jb.nn + b) * ROWS + row) * LD;
-        float2 x[N3];
 #pragma unroll
-        for (int j = 0; j < N3; ++j) x[j] = cmul(cconj(xn[j]), xm[j]);
-        fft::line<N3, true>(c_tw, x);
-        float2* dst = S1 + (p * N2 + r0 + row) * M3;
-#pragma unroll
-        for (int f = -F3; f <= F3; ++f) dst[f + F3] = x[(f + N3) % N3];
+      for (int a = 0; a < ACC; ++a) {                            // stage 3: x DFT at sphere points
+        const int idx = tid + a * THREADS;
+        if (idx < P * NG) {
+          const int p = idx / NG, t = idx - p * NG;
+          const int2 g = sg[t];
+          const float2 s = S2[(size_t)p * M2 * M3 + g.y];
+          acc[a] = cadd(acc[a], cmul(s, fft::tw<N1, true>(c_tw, g.x * j1)));
+        }
       }
     }
     __syncthreads();
-    for (int it = tid; it < P * M3; it += kThreads) {          // stage 2: y FFT of kept planes
-      const int p = it / M3, m3 = it - p * M3;
-      float2 y[N2];
-#pragma unroll
-      for (int j = 0; j < N2; ++j) y[j] = S1[(p * N2 + j) * M3 + m3];
-      fft::line<N2, true>(c_tw, y);
-#pragma unroll
-      for (int f = -F2; f <= F2; ++f) S2[(p * M2 + (f + F2)) * M3 + m3] = y[(f + N2) % N2];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < ACC; ++a) {                             // stage 3: x DFT at sphere points
-      const int idx = tid + a * kThreads;
-      if (idx < P * NG) {
-        const int p = idx / NG, t = idx - p * NG;
-        const int2 g = sg[t];
-        const float2 s = S2[p * M2 * M3 + g.y];
-        acc[a] = cadd(acc[a], cmul(s, fft::tw<N1, true>(c_tw, g.x * j1)));
-      }
-    }
   }
   const float inv = 1.0f / (float)(N1 * N2 * N3);
 #pragma unroll
   for (int a = 0; a < ACC; ++a) {
-    const int idx = tid + a * kThreads;
+    const int idx = tid + a * THREADS;
     if (idx < P * NG) {
       const int p = idx / NG, t = idx - p * NG;
-      jb.out[(size_t)p * d.ng_max + t] = make_float2(acc[a].x * inv, acc[a].y * inv);
+      int sa, sb;
+      float2* dst;
+      product_of(d, jb, p, sa, sb, dst);
+      dst[t] = make_float2(acc[a].x * inv, acc[a].y * inv);
     }
   }
 }
@@ -278,40 +372,46 @@ __global__ void dipole_kernel(DevSys d, const float2* __restrict__ coef, const d
 
 // ---------------------------------------------------------------- dispatch
 typedef void (*RsFn)(DevSys, const float2*, float2*);
-typedef void (*PairFn)(DevSys, const float2*, float2*, int, long long, long long);
+typedef void (*PairFn)(DevSys, const float2*, float2*, int, int, int, long long);
 
 struct Variant {
-  int n1, n2, n3, f1, f2, f3, pmax, bmax, ngmax;
+  int n1, n2, n3, f1, f2, f3, pmax, bmax, threads, acc;
+  bool merged;
   RsFn rs;
   size_t rs_smem;
   PairFn pair;
   size_t (*pair_smem)(int);
 };
 
-#define BSE_VARIANT(N1, N2, N3, F1, F2, F3, PMAX, BMAX, ROWS, ACC)                                              \
-  Variant {                                                                                                     \
-    N1, N2, N3, F1, F2, F3, PMAX, BMAX, (ACC) * kThreads / (PMAX), realspace_kernel<N1, N2, N3, F1, F2, F3>,    \
-        RsCfg<N1, N2, N3, F1, F2, F3>::smem, pair_kernel<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, ACC>,             \
-        PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, ACC>::smem                                                 \
+#define BSE_VARIANT(N1, N2, N3, F1, F2, F3, PMAX, BMAX, ROWS, ACC, THREADS, MERGED)                              \
+  Variant {                                                                                                      \
+    N1, N2, N3, F1, F2, F3, PMAX, BMAX, THREADS, ACC, MERGED, realspace_kernel<N1, N2, N3, F1, F2, F3>,          \
+        RsCfg<N1, N2, N3, F1, F2, F3>::smem,                                                                     \
+        pair_kernel<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, ACC, THREADS, MERGED>,                                 \
+        PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, ACC, THREADS, MERGED>::smem                                \
   }
 
 const Variant kVariants[] = {
-    BSE_VARIANT(8, 8, 8, 2, 2, 2, 16, 8, 8, 4),
-    BSE_VARIANT(24, 24, 24, 3, 3, 3, 16, 8, 12, 8),
-    BSE_VARIANT(32, 32, 32, 5, 5, 5, 16, 8, 16, 20),
-    BSE_VARIANT(48, 48, 48, 6, 6, 6, 16, 8, 16, 34),
-    BSE_VARIANT(12, 12, 48, 2, 2, 10, 9, 6, 12, 5),
+    BSE_VARIANT(8, 8, 8, 2, 2, 2, 18, 12, 8, 8, 128, true),          // small test cells
+    BSE_VARIANT(24, 24, 24, 3, 3, 3, 18, 12, 24, 5, 448, true),      // fcc 4x4x4, 3v3c
+    BSE_VARIANT(32, 32, 32, 5, 5, 5, 25, 14, 16, 19, 416, true),     // fcc 8x8x8, 3v4c
+    BSE_VARIANT(48, 48, 48, 6, 6, 6, 16, 8, 16, 34, 256, false),     // fcc 12x12x12, 4v4c
+    BSE_VARIANT(12, 12, 48, 2, 2, 10, 18, 12, 12, 10, 224, true),    // hexagonal sheets, <= 3v3c
 };
 
 const Variant* pick(const DevSys& d) {
-  const int pmax = (d.nv > d.nc ? d.nv : d.nc);
-  const int pm = (d.nv * d.nc > pmax * pmax) ? d.nv * d.nc : pmax * pmax;
+  const int vmax = d.nv > d.nc ? d.nv : d.nc;
   for (const Variant& v : kVariants) {
     if (v.n1 != d.n1 || v.n2 != d.n2 || v.n3 != d.n3) continue;
     const int f[3] = {v.f1, v.f2, v.f3};
     bool ok = true;
     for (int j = 0; j < 3; ++j) ok = ok && d.fwf[j] <= f[j] && d.fpair[j] <= f[j];
-    ok = ok && pm <= v.pmax && d.nb <= v.bmax && 2 * pmax <= v.bmax && (long long)pm * d.ng_max <= (long long)v.ngmax * v.pmax;
+    const int pd = v.merged ? d.nv * d.nv + d.nc * d.nc : vmax * vmax;
+    const int bd = v.merged ? 2 * d.nb : 2 * vmax;
+    const int px = d.nv * d.nc;
+    const int pm = pd > px ? pd : px;
+    ok = ok && pm <= v.pmax && bd <= v.bmax && d.nb <= v.bmax &&
+         (long long)pm * d.ng_max <= (long long)v.acc * v.threads;
     if (ok) return &v;
   }
   return nullptr;
@@ -341,22 +441,22 @@ int launch_pair_exchange(const DevSys& d, const void* u, void* rho_x, void* stre
   if (!v) return (int)cudaErrorInvalidValue;
   const size_t sm = v->pair_smem(d.ng_max);
   cudaFuncSetAttribute((const void*)v->pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  v->pair<<<d.nkpt, kThreads, sm, (cudaStream_t)stream>>>(d, (const float2*)u, (float2*)rho_x, 0, 0, 0);
+  v->pair<<<d.nkpt, v->threads, sm, (cudaStream_t)stream>>>(d, (const float2*)u, (float2*)rho_x, 0, 0, 0, 0);
   return (int)cudaGetLastError();
 }
 
-int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, long long b_begin, long long b_count,
-                       long long vbase, void* stream) {
+int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, int q_begin, int q_end, long long vbase,
+                       void* stream) {
   const Variant* v = pick(d);
   if (!v) return (int)cudaErrorInvalidValue;
   const size_t sm = v->pair_smem(d.ng_max);
   cudaFuncSetAttribute((const void*)v->pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  for (long long done = 0; done < b_count;) {
-    const long long chunk = (b_count - done) > (1LL << 29) ? (1LL << 29) : (b_count - done);
-    v->pair<<<(unsigned)(2 * chunk), kThreads, sm, (cudaStream_t)stream>>>(d, (const float2*)u, (float2*)rho_dir, 1,
-                                                                           b_begin + done, vbase);
-    done += chunk;
-  }
+  const int nqc = q_end - q_begin;
+  const long long ntk = (d.nkpt + kTK - 1) / kTK, ntq = (nqc + kTQ - 1) / kTQ;
+  const long long cells = ntq * ntk * kTQ * kTK * (v->merged ? 1 : 2);
+  if (cells >= (1LL << 31)) return (int)cudaErrorInvalidValue;
+  v->pair<<<(unsigned)cells, v->threads, sm, (cudaStream_t)stream>>>(d, (const float2*)u, (float2*)rho_dir, 1,
+                                                                     q_begin, nqc, vbase);
   return (int)cudaGetLastError();
 }
 

@@ -237,6 +237,11 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
     const int packed = (r[3] + 1) | ((r[4] + 1) << 2) | ((r[5] + 1) << 4);
     h_blocks[i] = make_int4(r[0], r[1], r[2], packed);
   }
+  std::vector<int> h_blkidx((size_t)nkpt * nkpt, -1);
+  for (long long i = 0; i < d.nblocks; ++i) {
+    const int32_t* r = &sp.blocks[6 * i];
+    h_blkidx[(size_t)r[2] * nkpt + r[0]] = (int)i;
+  }
   std::vector<float> h_xs(ng_max, 0.0f);
   for (int t = 1; t < d.ng0; ++t) {
     const int* g = &sp.gq[0][3 * t];
@@ -263,6 +268,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   const size_t o_qvo = off; off = align256(off + sp.qvec_off.size() * sizeof(long long));
   const size_t o_kgq = off; off = align256(off + h_kgq.size() * sizeof(double));
   const size_t o_xs = off; off = align256(off + h_xs.size() * sizeof(float));
+  const size_t o_bi = off; off = align256(off + h_blkidx.size() * sizeof(int));
   char* base = nullptr;
   bse_status st = cuda_check(cudaMalloc((void**)&base, off), "cudaMalloc(plan tables)");
   if (st != BSE_OK) return st;
@@ -278,6 +284,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   if (!err) err = up(o_qvo, sp.qvec_off.data(), sp.qvec_off.size() * sizeof(long long));
   if (!err) err = up(o_kgq, h_kgq.data(), h_kgq.size() * sizeof(double));
   if (!err) err = up(o_xs, h_xs.data(), h_xs.size() * sizeof(float));
+  if (!err) err = up(o_bi, h_blkidx.data(), h_blkidx.size() * sizeof(int));
   if ((st = cuda_check(err, "cudaMemcpy(plan tables)")) != BSE_OK) return st;
   d.gk = (const char4*)(base + o_gk);
   d.npw = (const int*)(base + o_npw);
@@ -288,6 +295,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   d.qvec_off = (const long long*)(base + o_qvo);
   d.kgq = (const double*)(base + o_kgq);
   d.xscale = (const float*)(base + o_xs);
+  d.blkidx = (const int*)(base + o_bi);
   return BSE_OK;
 }
 
@@ -459,8 +467,8 @@ bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags, const void*
   }
   if (flags & BSE_PD_DIRECT) {
     if (!rho_dir || q_begin < 0 || q_end > d.nq || q_begin >= q_end) return set_error(BSE_ERR_ARG, "bad direct range");
-    const long long b0 = sp.qblk_off[q_begin], nb = sp.qblk_off[q_end] - b0, vb = sp.qvec_off[q_begin];
-    if ((st = cuda_check(launch_pair_direct(d, ws, rho_dir, b0, nb, vb, stream), "pair direct")) != BSE_OK)
+    const long long vb = sp.qvec_off[q_begin];
+    if ((st = cuda_check(launch_pair_direct(d, ws, rho_dir, q_begin, q_end, vb, stream), "pair direct")) != BSE_OK)
       return st;
   }
   return BSE_OK;
