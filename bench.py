@@ -235,7 +235,7 @@ def run_stage(args):
 
     spec, s = make_inputs(args.config)
     plan = bse.Plan([spec])
-    qchunk = args.qchunk or (16 if args.only == "pair" else None)
+    qchunk = args.qchunk or (16 if args.only == "pair" else 32)
     F = Forward(plan, 0, nsteps=spec.nsteps, nw=spec.nw, qchunk=qchunk)
     dev = torch.device("cuda")
     coef = torch.as_tensor(s.coef.astype(np.complex64), device=dev)
