@@ -216,6 +216,27 @@ bse_status bse_spectrum(bse_plan* plan, int s, const void* H, const void* P, int
                         void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * bse_spectrum without a caller workspace.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc when they run the
+ * spectrum - for example code behind a foreign-function boundary that is handed
+ * only the input and output buffers by a host framework that owns all device
+ * memory.  The scratch (Krylov basis, projection partials, barrier words) is a
+ * 48 MiB file-scope device array inside the library, held on every device that
+ * loads the library until the process exits; no memory is allocated by this
+ * call.  Arguments and outputs are those of bse_spectrum.
+ * Limit: the scratch bse_workspace_size(BSE_WS_SPECTRUM, nsteps) reports must
+ * fit in 48 MiB (roughly nsteps * dim * 16 bytes + nsteps * 16 KiB); larger
+ * requests return BSE_ERR_ARG with the sizes in bse_last_error().
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call shares
+ * the one array and it keeps the last call's contents (the words that must
+ * start at zero are cleared by each call): calls that overlap on the GPU race.
+ */
+bse_status bse_spectrum_static(bse_plan* plan, int s, const void* H, const void* P, int nsteps,
+                               const double* omega, int nw, double eta,
+                               double* eps2, double* ab, int* steps_done, void* stream);
+
+/*
  * A9.  Adjoint of L(eps_2) given dL_deps2 float64 [nw].  Recomputes the
  * Lanczos basis, forms G_H = -C sum_w g(w) i xt(w) x(w)^H from the Krylov
  * resolvent (x = R(z)P, xt = R(conj z)P), and chains it:

@@ -26,7 +26,7 @@ BSE_BK_INIT, BSE_BK_DIRECT = 1, 2
 EXPORTED = [
     "bse_last_error", "bse_plan_create", "bse_plan_create_host", "bse_plan_destroy", "bse_plan_info", "bse_gvectors",
     "bse_pair_blocks", "bse_workspace_size", "bse_rho_dir_count", "bse_pair_densities",
-    "bse_build_kernel", "bse_apply_H", "bse_spectrum", "bse_spectrum_backward", "bse_status_read",
+    "bse_build_kernel", "bse_apply_H", "bse_spectrum", "bse_spectrum_static", "bse_spectrum_backward", "bse_status_read",
 ]
 
 
@@ -76,6 +76,7 @@ def load():
     lib.bse_build_kernel.argtypes = [vp, i, u, vp, vp, i, i, vp, vp, d, i, vp, vp, sz, vp]
     lib.bse_apply_H.argtypes = [vp, i, vp, vp, vp, i, vp]
     lib.bse_spectrum.argtypes = [vp, i, vp, vp, i, vp, i, d, vp, vp, vp, vp, sz, vp]
+    lib.bse_spectrum_static.argtypes = [vp, i, vp, vp, i, vp, i, d, vp, vp, vp, vp]
     lib.bse_spectrum_backward.argtypes = [vp, i, vp, vp, i, vp, i, d, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.bse_status_read.argtypes = [vp, vp]
     for name in EXPORTED:
@@ -213,6 +214,11 @@ def bse_spectrum(plan, s, H, P, nsteps, omega, eta, eps2, ab, steps_done, ws):
     _check(load().bse_spectrum(plan.handle, s, _ptr(H), _ptr(P), int(nsteps), _ptr(omega), omega.numel(),
                                float(eta), _ptr(eps2), _ptr(ab), _ptr(steps_done), _ptr(ws), _nbytes(ws),
                                _stream()))
+
+
+def bse_spectrum_static(plan, s, H, P, nsteps, omega, eta, eps2, ab, steps_done):
+    _check(load().bse_spectrum_static(plan.handle, s, _ptr(H), _ptr(P), int(nsteps), _ptr(omega), omega.numel(),
+                                      float(eta), _ptr(eps2), _ptr(ab), _ptr(steps_done), _stream()))
 
 
 def bse_spectrum_backward(plan, s, H, P, nsteps, omega, eta, dL_deps2, rho_x, rho_dir, W, dL_ddelta, dL_dH,

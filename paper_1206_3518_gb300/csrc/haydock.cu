@@ -14,6 +14,8 @@
 // BSE_ERR_TIMEOUT in the plan status word and the kernel returns).
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace bse {
@@ -449,6 +451,46 @@ int run_haydock(const DevSys& d, const void* H, const void* P, int nsteps, const
 
 int launch_spectrum(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw,
                     double eta, double* eps2, double* ab, int* steps_done, void* ws, int* status, void* stream) {
+  return run_haydock(d, H, P, nsteps, omega, nw, eta, eps2, ab, steps_done, ws, status, stream, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Spectrum with library-owned scratch, for callers that cannot allocate device
+// memory themselves.  The scratch is one file-scope device array of fixed size;
+// every device that loads this library holds it until the process exits.  Host
+// code may not pass the array's name to a kernel (in host code it is only a
+// stand-in for the symbol), so its device address is looked up once per device
+// with cudaGetSymbolAddress and cached.  All calls share the array: calls that
+// overlap on the GPU race on it.
+namespace {
+constexpr size_t kStaticScratchBytes = size_t(48) << 20;
+static __device__ __align__(256) unsigned char g_spectrum_scratch[kStaticScratchBytes];
+constexpr int kMaxDevices = 256;
+void* g_scratch_addr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mu;
+}  // namespace
+
+size_t spectrum_static_capacity() { return kStaticScratchBytes; }
+
+int launch_spectrum_static(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw,
+                           double eta, double* eps2, double* ab, int* steps_done, int* status, void* stream) {
+  int dev = 0;
+  int e = (int)cudaGetDevice(&dev);
+  if (e) return e;
+  if (dev < 0 || dev >= kMaxDevices) return (int)cudaErrorInvalidDevice;
+  void* ws = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+      void* p = nullptr;
+      e = (int)cudaGetSymbolAddress(&p, g_spectrum_scratch);
+      if (e) return e;
+      g_scratch_addr[dev] = p;
+    }
+    ws = g_scratch_addr[dev];
+  }
+  // The barrier words are cleared by run_haydock before the launch; every other
+  // scratch word is written before it is read.
   return run_haydock(d, H, P, nsteps, omega, nw, eta, eps2, ab, steps_done, ws, status, stream, nullptr);
 }
 

@@ -67,6 +67,9 @@ int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin
                                void* H, void* ws, void* stream);
 size_t kernel_ws_bytes(const DevSys& d, long long qchunk);
 
+size_t spectrum_static_capacity();
+int launch_spectrum_static(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw,
+                           double eta, double* eps2, double* ab, int* steps_done, int* status, void* stream);
 int launch_apply_h(const DevSys& d, const void* H, const void* X, void* Y, int nvec, void* stream);
 size_t spectrum_ws_bytes(const DevSys& d, long long nsteps);
 int launch_spectrum(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw,

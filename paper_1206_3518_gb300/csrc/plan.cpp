@@ -526,6 +526,24 @@ bse_status bse_spectrum(bse_plan* plan, int s, const void* H, const void* P, int
   return cuda_check(e, "spectrum");
 }
 
+bse_status bse_spectrum_static(bse_plan* plan, int s, const void* H, const void* P, int nsteps, const double* omega,
+                               int nw, double eta, double* eps2, double* ab, int* steps_done, void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const DevSys& d = plan->sys[s].d;
+  if (!H || !P || !omega || !eps2 || !ab || !steps_done || nsteps < 1 || nw < 0 || !(eta > 0.0))
+    return set_error(BSE_ERR_ARG, "spectrum needs H, P, omega, eps2, ab, steps_done, nsteps >= 1, eta > 0");
+  if (nsteps > d.dim) return set_error(BSE_ERR_ARG, "nsteps > dim");
+  const size_t need = spectrum_ws_bytes(d, nsteps);
+  if (need > spectrum_static_capacity())
+    return set_error(BSE_ERR_ARG, "scratch of " + std::to_string(need) + " bytes exceeds the library's static " +
+                                      std::to_string(spectrum_static_capacity()) +
+                                      "-byte spectrum scratch; use bse_spectrum with a caller workspace");
+  const int e = launch_spectrum_static(d, H, P, nsteps, omega, nw, eta, eps2, ab, steps_done, plan->d_status, stream);
+  if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "cooperative launch not possible on this device");
+  return cuda_check(e, "spectrum (static scratch)");
+}
+
 bse_status bse_spectrum_backward(bse_plan* plan, int s, const void* H, const void* P, int nsteps,
                                  const double* omega, int nw, double eta, const double* dL_deps2,
                                  const void* rho_x, const void* rho_dir, const void* W, double* dL_ddelta,
