@@ -15,68 +15,15 @@
 // sum_k opA(A[m][k]) B[n][k] with both operands K-contiguous.
 #include <cuda_runtime.h>
 
+#include "gemm_tile.cuh"
 #include "internal.h"
 
 namespace bse {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, kGemmThreads = 256;
-
-__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// One 64x64 output tile of C = opA(A) B^T over K, accumulated in registers (4x4 per thread).
-// A: [M][lda], B: [N][ldb] float2, K-contiguous.  Optional per-k scale applied to both.
-template <bool CONJ_A, bool SCALE>
-__device__ __forceinline__ void tile_nt(const float2* __restrict__ A, int lda, int M, const float2* __restrict__ B,
-                                        int ldb, int N, int K, const float* __restrict__ kscale, int m0, int n0,
-                                        float2 (&acc)[4][4]) {
-  __shared__ float2 As[BK][BM + 1];
-  __shared__ float2 Bs[BK][BN + 1];
-  const int t = threadIdx.x;
-  const int lk = t % BK, lr = t / BK;          // loader: 16 rows x 16 k per pass
-  const int tm = t / 16, tn = t % 16;          // compute: rows tm*4.., cols tn*4..
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
-  for (int k0 = 0; k0 < K; k0 += BK) {
-    const int kk = k0 + lk;
-    const float sc = (SCALE && kk < K) ? kscale[kk] : 1.0f;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = lr + 16 * i;
-      float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-      if (kk < K && m0 + r < M) a = A[(size_t)(m0 + r) * lda + kk];
-      if (kk < K && n0 + r < N) b = B[(size_t)(n0 + r) * ldb + kk];
-      if (CONJ_A) a.y = -a.y;
-      if (SCALE) {
-        a.x *= sc; a.y *= sc;
-        b.x *= sc; b.y *= sc;
-      }
-      As[lk][r] = a;
-      Bs[lk][r] = b;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < BK; ++k) {
-      float2 av[4], bv[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[k][tm * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tn * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          acc[i][j].x = fmaf(av[i].x, bv[j].x, fmaf(-av[i].y, bv[j].y, acc[i][j].x));
-          acc[i][j].y = fmaf(av[i].x, bv[j].y, fmaf(av[i].y, bv[j].x, acc[i][j].y));
-        }
-    }
-    __syncthreads();
-  }
-}
+using gemm::BM;
+using gemm::BN;
+constexpr int kGemmThreads = gemm::kThreads;
 
 __device__ __forceinline__ int kpt_of_pair(const DevSys& d, int S) { return S / (d.nv * d.nc); }
 
@@ -86,11 +33,11 @@ __global__ __launch_bounds__(kGemmThreads) void init_kernel(DevSys d, const floa
                                                             float2* __restrict__ H) {
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   if (m0 >= d.dim || n0 >= d.dim) return;
-  const int mlast = min(m0 + BM, d.dim) - 1;
   if (kpt_of_pair(d, m0) > kpt_of_pair(d, min(n0 + BN, d.dim) - 1)) return;   // strictly lower block triangle
-  (void)mlast;
+  __shared__ gemm::Smem sm;
   float2 acc[4][4];
-  tile_nt<true, true>(rho_x, d.ng_max, d.dim, rho_x, d.ng_max, d.dim, d.ng0, d.xscale, m0, n0, acc);
+  gemm::tile<true, true, true, false, true>(rho_x, d.ng_max, d.dim, rho_x, d.ng_max, d.dim, d.ng0, m0, n0, sm, acc,
+                                            d.xscale);
   const int tm = threadIdx.x / 16, tn = threadIdx.x % 16;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -126,8 +73,9 @@ __global__ __launch_bounds__(kGemmThreads) void gemm_wr(DevSys d, const float2* 
   const float2* A = rho_dir + (size_t)aoff * d.ng_max;
   const float2* B = W + (size_t)q * d.ng_max * d.ng_max;
   float2* C = X + (size_t)((d.qblk_off[q] - b0) * w) * d.ng_max;
+  __shared__ gemm::Smem sm;
   float2 acc[4][4];
-  tile_nt<false, false>(A, d.ng_max, M, B, d.ng_max, NG, NG, nullptr, m0, n0, acc);
+  gemm::tile<true, true, false, false>(A, d.ng_max, M, B, d.ng_max, NG, NG, m0, n0, sm, acc);
   const int tm = threadIdx.x / 16, tn = threadIdx.x % 16;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -230,6 +178,14 @@ int launch_kernel_init(const DevSys& d, const void* rho_x, const double* energie
                        void* stream) {
   dim3 grid((d.dim + BN - 1) / BN, (d.dim + BM - 1) / BM);
   init_kernel<<<grid, kGemmThreads, 0, (cudaStream_t)stream>>>(d, (const float2*)rho_x, energies, delta, (float2*)H);
+  return (int)cudaGetLastError();
+}
+
+int launch_gemm_wr(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long vbase, long long max_rows,
+                   const void* W, void* X, int side_c, void* stream) {
+  dim3 grid((d.ng_max + BN - 1) / BN, (unsigned)((max_rows + BM - 1) / BM), q_end - q_begin);
+  gemm_wr<<<grid, kGemmThreads, 0, (cudaStream_t)stream>>>(d, (const float2*)rho_dir, (const float2*)W, (float2*)X,
+                                                          q_begin, vbase, side_c);
   return (int)cudaGetLastError();
 }
 

@@ -66,6 +66,8 @@ int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin
                                long long b_count, long long vbase, long long max_rows, const void* W, int prec,
                                void* H, void* ws, void* stream);
 size_t kernel_ws_bytes(const DevSys& d, long long qchunk);
+int launch_gemm_wr(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long vbase, long long max_rows,
+                   const void* W, void* X, int side_c, void* stream);
 
 size_t spectrum_static_capacity();
 int launch_spectrum_static(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw,
@@ -75,10 +77,10 @@ size_t spectrum_ws_bytes(const DevSys& d, long long nsteps);
 int launch_spectrum(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw,
                     double eta, double* eps2, double* ab, int* steps_done, void* ws, int* status, void* stream);
 size_t backward_ws_bytes(const DevSys& d, long long nsteps);
-int launch_backward(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw,
-                    double eta, const double* dL, const void* rho_x, const void* rho_dir, const void* W,
-                    double* d_delta, void* dH, void* drho_x, void* drho_dir, void* dW, void* ws, int* status,
-                    void* stream);
+int launch_backward(const DevSys& d, const long long* h_qblk_off, const long long* h_qvec_off, const void* H,
+                    const void* P, int nsteps, const double* omega, int nw, double eta, const double* dL,
+                    const void* rho_x, const void* rho_dir, const void* W, double* d_delta, void* dH, void* drho_x,
+                    void* drho_dir, void* dW, void* ws, int* status, void* stream);
 int upload_twiddles();
 int run_haydock(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw, double eta,
                 double* eps2, double* ab, int* steps_done, void* ws, int* status, void* stream, double2** V_out);

@@ -555,11 +555,13 @@ bse_status bse_spectrum_backward(bse_plan* plan, int s, const void* H, const voi
   if (!H || !P || !omega || !dL_deps2 || !dL_ddelta || nsteps < 1 || nw < 1 || !(eta > 0.0))
     return set_error(BSE_ERR_ARG, "backward needs H, P, omega, dL_deps2, dL_ddelta, nsteps >= 1, eta > 0");
   if (nsteps > d.dim) return set_error(BSE_ERR_ARG, "nsteps > dim");
-  if ((dL_drho_x && !rho_x) || ((dL_drho_dir || dL_dW) && (!rho_dir || !W)) || (dL_drho_x && !W && false))
+  if ((dL_drho_x && !rho_x) || ((dL_drho_dir || dL_dW) && (!rho_dir || !W)))
     return set_error(BSE_ERR_ARG, "chained gradients need their forward inputs");
   if (!ws || ws_bytes < backward_ws_bytes(d, nsteps)) return set_error(BSE_ERR_WORKSPACE, "backward workspace too small");
-  const int e = launch_backward(d, H, P, nsteps, omega, nw, eta, dL_deps2, rho_x, rho_dir, W, dL_ddelta, dL_dH,
-                                dL_drho_x, dL_drho_dir, dL_dW, ws, plan->d_status, stream);
+  const SysPlan& sp = plan->sys[s];
+  const int e = launch_backward(d, sp.qblk_off.data(), sp.qvec_off.data(), H, P, nsteps, omega, nw, eta, dL_deps2,
+                                rho_x, rho_dir, W, dL_ddelta, dL_dH, dL_drho_x, dL_drho_dir, dL_dW, ws,
+                                plan->d_status, stream);
   if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "cooperative launch not possible on this device");
   return cuda_check(e, "spectrum backward");
 }
