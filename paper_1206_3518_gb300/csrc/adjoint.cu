@@ -148,13 +148,14 @@ __global__ void finish_m_kernel(const double* __restrict__ Mh, int nsteps, const
   }
 }
 
-__global__ void v_to_float_kernel(const double2* __restrict__ V, long long n, const int* __restrict__ done, int dim,
+// Vf = FP32 basis (the hi parts of the double-float split), zero beyond the steps done.
+__global__ void v_to_float_kernel(const float4* __restrict__ V, long long n, const int* __restrict__ done, int dim,
                                   float2* __restrict__ Vf) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int j = (int)(i / dim);
-  const double2 v = V[i];
-  Vf[i] = (j < *done) ? make_float2((float)v.x, (float)v.y) : make_float2(0.f, 0.f);
+  const float4 v = V[i];
+  Vf[i] = (j < *done) ? make_float2(v.x + v.y, v.z + v.w) : make_float2(0.f, 0.f);
 }
 
 // Generic grouped product C = opA(A) opB(B)^T with per-column epilogue scale (dense, one group).
@@ -284,8 +285,7 @@ __global__ __launch_bounds__(256) void block_grad_kernel(DevSys d, const float2*
 
 size_t backward_ws_bytes(const DevSys& d, long long nsteps) { return bwd_layout(d, nsteps).total; }
 
-int run_haydock(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw, double eta,
-                double* eps2, double* ab, int* steps_done, void* ws, int* status, void* stream, double2** V_out);
+
 
 int launch_backward(const DevSys& d, const long long* h_qblk_off, const long long* h_qvec_off, const void* H,
                     const void* P, int nsteps, const double* omega, int nw, double eta, const double* dL,
@@ -303,7 +303,7 @@ int launch_backward(const DevSys& d, const long long* h_qblk_off, const long lon
   float2* Vf = (float2*)(base + L.Vf);
   float2* Zf = (float2*)(base + L.Zf);
   float2* Gh = dH ? (float2*)dH : (float2*)(base + L.Gh);
-  double2* V = nullptr;
+  float4* V = nullptr;
   // 1. Lanczos recomputed (the spectrum it evaluates on the first frequencies is not used).
   int e = run_haydock(d, H, P, nsteps, omega, nw < kNwChunk ? nw : kNwChunk, eta, (double*)(base + L.eps2), ab, done,
                       base + L.spec, status, stream, &V);

@@ -7,6 +7,13 @@
 // twice per step (FP64 basis and recurrence); the matrix-vector product reads
 // H in FP32, multiplies in FP32 and combines 16-element partial sums in FP64.
 //
+// GB300's FP64 pipes are narrow, so the O(j dim) work of each step (projections and
+// updates against the basis) runs in double-float arithmetic on the FP32 pipes: the basis
+// is stored split (hi, lo) per component, products are made error-free with FMA and sums
+// carried with TwoSum (about 46 significant bits, orthogonality ~1e-13), and the
+// matrix-vector product keeps compensated FP32 partial sums.  Only O(dim) per step and
+// the coefficient reductions use native FP64.
+//
 // One persistent cooperative launch runs every step.  Each CTA owns a
 // contiguous slice of rows for the product, the projections and the updates,
 // so the only global exchanges are the projection coefficients and two norms
@@ -92,11 +99,74 @@ __device__ __forceinline__ float2 load_x1(const double2* x, int i) {
   return make_float2((float)a.x, (float)a.y);
 }
 
-// Row dot  sum_c H[r][c] x[c]: FP32 products accumulated over 16 elements per lane,
-// then combined in FP64 (vector loads of H when dim is even).
+// ---------------------------------------------------------------- double-float helpers
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// acc (hi, lo) += a * b with a, b given as (hi, lo); the error of the leading product is exact (FMA).
+__device__ __forceinline__ void df_mac(float2& acc, float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  float s, t;
+  two_sum(acc.x, p, s, t);
+  acc.x = s;
+  acc.y += t + e;
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void df_add(float2& acc, float2 a) {
+  float s, t;
+  two_sum(acc.x, a.x, s, t);
+  acc.x = s;
+  acc.y += t + a.y;
+}
+__device__ __forceinline__ float2 df_norm(float2 a) {   // renormalise so |lo| <= ulp(hi)/2
+  const float s = a.x + a.y;
+  return make_float2(s, a.y - (s - a.x));
+}
+__device__ __forceinline__ float2 df_split(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+__device__ __forceinline__ double df_val(float2 a) { return (double)a.x + (double)a.y; }
+// complex double-float element: (re.hi, re.lo, im.hi, im.lo)
+__device__ __forceinline__ float4 cdf_split(double2 z) {
+  const float2 r = df_split(z.x), i = df_split(z.y);
+  return make_float4(r.x, r.y, i.x, i.y);
+}
+__device__ __forceinline__ double2 cdf_val(float4 z) {
+  return make_double2(df_val(make_float2(z.x, z.y)), df_val(make_float2(z.z, z.w)));
+}
+__device__ __forceinline__ float4 df_shfl_xor(float4 v, int o) {
+  return make_float4(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o),
+                     __shfl_xor_sync(0xffffffffu, v.z, o), __shfl_xor_sync(0xffffffffu, v.w, o));
+}
+__device__ __forceinline__ float4 cdf_warp_sum(float4 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float4 u = df_shfl_xor(v, o);
+    float2 re = make_float2(v.x, v.y), im = make_float2(v.z, v.w);
+    df_add(re, make_float2(u.x, u.y));
+    df_add(im, make_float2(u.z, u.w));
+    re = df_norm(re);
+    im = df_norm(im);
+    v = make_float4(re.x, re.y, im.x, im.y);
+  }
+  return v;
+}
+
+// Row dot  sum_c H[r][c] x[c]: FP32 products over 16 elements per lane, then carried
+// in a compensated (hi, lo) FP32 sum; one FP64 combine per row.
 template <typename XT>
 __device__ __forceinline__ double2 row_dot(const float2* __restrict__ Hr, const XT* x, int dim, int lane) {
-  double2 acc = make_double2(0.0, 0.0);
+  float2 ar = make_float2(0.f, 0.f), ai = make_float2(0.f, 0.f);
+  auto carry = [&](float2 s) {
+    df_add(ar, make_float2(s.x, 0.f));
+    df_add(ai, make_float2(s.y, 0.f));
+  };
   if ((dim & 1) == 0) {
     const float4* h4 = reinterpret_cast<const float4*>(Hr);
     const int n4 = dim >> 1;
@@ -112,8 +182,7 @@ __device__ __forceinline__ double2 row_dot(const float2* __restrict__ Hr, const 
         s.x = fmaf(h.z, v.z, fmaf(-h.w, v.w, s.x));
         s.y = fmaf(h.z, v.w, fmaf(h.w, v.z, s.y));
       }
-      acc.x += s.x;
-      acc.y += s.y;
+      carry(s);
     }
     float2 s = make_float2(0.f, 0.f);
     for (; i < n4; i += 32) {
@@ -124,8 +193,7 @@ __device__ __forceinline__ double2 row_dot(const float2* __restrict__ Hr, const 
       s.x = fmaf(h.z, v.z, fmaf(-h.w, v.w, s.x));
       s.y = fmaf(h.z, v.w, fmaf(h.w, v.z, s.y));
     }
-    acc.x += s.x;
-    acc.y += s.y;
+    carry(s);
   } else {
     int i = lane;
     for (; i + 32 * 15 < dim; i += 32 * 16) {
@@ -137,8 +205,7 @@ __device__ __forceinline__ double2 row_dot(const float2* __restrict__ Hr, const 
         s.x = fmaf(h.x, v.x, fmaf(-h.y, v.y, s.x));
         s.y = fmaf(h.x, v.y, fmaf(h.y, v.x, s.y));
       }
-      acc.x += s.x;
-      acc.y += s.y;
+      carry(s);
     }
     float2 s = make_float2(0.f, 0.f);
     for (; i < dim; i += 32) {
@@ -147,10 +214,10 @@ __device__ __forceinline__ double2 row_dot(const float2* __restrict__ Hr, const 
       s.x = fmaf(h.x, v.x, fmaf(-h.y, v.y, s.x));
       s.y = fmaf(h.x, v.y, fmaf(h.y, v.x, s.y));
     }
-    acc.x += s.x;
-    acc.y += s.y;
+    carry(s);
   }
-  return warp_sum(acc);
+  const float4 t = cdf_warp_sum(make_float4(ar.x, ar.y, ai.x, ai.y));
+  return cdf_val(t);
 }
 
 struct HayArgs {
@@ -164,9 +231,9 @@ struct HayArgs {
   double* eps2;
   double* ab;
   int* steps_done;
-  double2* V;       // [nsteps][dim]
-  float2* vf;       // [dim]
-  double2* hpart;   // [grid][nsteps]
+  float4* V;        // [nsteps][dim] basis, double-float split (re.hi, re.lo, im.hi, im.lo)
+  float2* vf;       // [dim] FP32 copy of the current basis vector
+  double2* hpart;   // [grid][nsteps] per-CTA projection partials
   double2* h1;      // [nsteps]
   double2* h2;      // [nsteps]
   double* npart;    // [grid][2]
@@ -174,24 +241,29 @@ struct HayArgs {
   int* status;
 };
 
-// hpart[cta][i] = sum over own rows conj(V[i][r]) w[r], i in [0, n).
-__device__ void project_partial(const HayArgs& A, const double2* wsm, int row0, int nrows, int n) {
+// hpart[cta][i] = sum over own rows conj(V[i][r]) w[r], i in [0, n) (double-float products).
+__device__ void project_partial(const HayArgs& A, const float4* wsm, int row0, int nrows, int n) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int dim = A.d.dim;
   for (int i = warp; i < n; i += kWarps) {
-    const double2* Vi = A.V + (size_t)i * dim + row0;
-    double2 s = make_double2(0.0, 0.0);
+    const float4* Vi = A.V + (size_t)i * dim + row0;
+    float2 sr = make_float2(0.f, 0.f), si = make_float2(0.f, 0.f);
     for (int r = lane; r < nrows; r += 32) {
-      const double2 v = __ldcg(Vi + r), w = wsm[r];
-      s.x += v.x * w.x + v.y * w.y;
-      s.y += v.x * w.y - v.y * w.x;
+      const float4 v = __ldcg(Vi + r), w = wsm[r];
+      const float2 vr = make_float2(v.x, v.y), vi = make_float2(v.z, v.w);
+      const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
+      // conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr)
+      df_mac(sr, vr, wr);
+      df_mac(sr, vi, wi);
+      df_mac(si, vr, wi);
+      df_mac(si, df_neg(vi), wr);
     }
-    s = warp_sum(s);
-    if (lane == 0) A.hpart[(size_t)blockIdx.x * A.nsteps + i] = s;
+    const float4 t = cdf_warp_sum(make_float4(sr.x, sr.y, si.x, si.y));
+    if (lane == 0) A.hpart[(size_t)blockIdx.x * A.nsteps + i] = cdf_val(t);
   }
 }
 
-// h[i] = sum_cta hpart[cta][i] for the i owned by this CTA (deterministic order).
+// h[i] = sum_cta hpart[cta][i] for the i owned by this CTA (deterministic order, FP64).
 __device__ void reduce_coeffs(const HayArgs& A, double2* h, int n) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = blockIdx.x + gridDim.x * warp; i < n; i += gridDim.x * kWarps) {
@@ -206,33 +278,45 @@ __device__ void reduce_coeffs(const HayArgs& A, double2* h, int n) {
   }
 }
 
-// w[r] -= sum_i V[i][r] h[i] over own rows; warps split i, lanes split rows.
-__device__ void subtract_projection(const HayArgs& A, double2* wsm, double2 (*red)[32], const double2* h, int row0,
-                                    int nrows, int n) {
+// w[r] -= sum_i V[i][r] h[i] over own rows; warps split i, lanes split rows; h staged split in hs.
+__device__ void subtract_projection(const HayArgs& A, float4* wsm, float4 (*red)[32], float4* hs, const double2* h,
+                                    int row0, int nrows, int n) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int dim = A.d.dim;
+  for (int i = threadIdx.x; i < n; i += kThreads) hs[i] = cdf_split(__ldcg(h + i));
+  __syncthreads();
   for (int r0 = 0; r0 < nrows; r0 += 32) {
     const int r = r0 + lane;
-    double2 s = make_double2(0.0, 0.0);
+    float2 sr = make_float2(0.f, 0.f), si = make_float2(0.f, 0.f);
     if (r < nrows) {
       for (int i = warp; i < n; i += kWarps) {
-        const double2 v = __ldcg(A.V + (size_t)i * dim + row0 + r);
-        const double2 c = __ldcg(h + i);
-        s.x += v.x * c.x - v.y * c.y;
-        s.y += v.x * c.y + v.y * c.x;
+        const float4 v = __ldcg(A.V + (size_t)i * dim + row0 + r);
+        const float4 c = hs[i];
+        const float2 vr = make_float2(v.x, v.y), vi = make_float2(v.z, v.w);
+        const float2 cr = make_float2(c.x, c.y), ci = make_float2(c.z, c.w);
+        // v c = (vr cr - vi ci) + i (vr ci + vi cr)
+        df_mac(sr, vr, cr);
+        df_mac(sr, df_neg(vi), ci);
+        df_mac(si, vr, ci);
+        df_mac(si, vi, cr);
       }
     }
-    red[warp][lane] = s;
+    red[warp][lane] = make_float4(sr.x, sr.y, si.x, si.y);
     __syncthreads();
     if (warp == 0 && r < nrows) {
-      double2 t = make_double2(0.0, 0.0);
+      float2 tr = make_float2(0.f, 0.f), ti = make_float2(0.f, 0.f);
 #pragma unroll
       for (int q = 0; q < kWarps; ++q) {
-        t.x += red[q][lane].x;
-        t.y += red[q][lane].y;
+        df_add(tr, make_float2(red[q][lane].x, red[q][lane].y));
+        df_add(ti, make_float2(red[q][lane].z, red[q][lane].w));
       }
-      wsm[r].x -= t.x;
-      wsm[r].y -= t.y;
+      const float4 w = wsm[r];
+      float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
+      df_add(wr, df_neg(tr));
+      df_add(wi, df_neg(ti));
+      wr = df_norm(wr);
+      wi = df_norm(wi);
+      wsm[r] = make_float4(wr.x, wr.y, wi.x, wi.y);
     }
     __syncthreads();
   }
@@ -263,8 +347,10 @@ __device__ double all_cta_sum(const HayArgs& A, int which, double* red1) {
 }
 
 __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(HayArgs A) {
-  extern __shared__ double2 wsm[];                 // own rows of w
-  __shared__ double2 red[kWarps][32];
+  extern __shared__ float4 dyn[];
+  float4* wsm = dyn;                                // own rows of w (double-float)
+  float4* hs = dyn + ((A.d.dim + gridDim.x - 1) / gridDim.x);   // projection coefficients (double-float)
+  __shared__ float4 red[kWarps][32];
   __shared__ double red1[kWarps];
   const int dim = A.d.dim;
   const int rows_per = (dim + gridDim.x - 1) / gridDim.x;
@@ -286,7 +372,7 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(HayArgs A) {
   for (int r = threadIdx.x; r < nrows; r += kThreads) {
     const double2 p = A.P[row0 + r];
     const double2 v = make_double2(p.x * pinv, p.y * pinv);
-    A.V[row0 + r] = v;
+    A.V[row0 + r] = cdf_split(v);
     A.vf[row0 + r] = make_float2((float)v.x, (float)v.y);
   }
   if (!grid_barrier(A.bar, A.status)) return;
@@ -298,7 +384,7 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(HayArgs A) {
     for (int r = warp; r < nrows; r += kWarps) {
       const double2 s = row_dot(A.H + (size_t)(row0 + r) * dim, A.vf, dim, lane);
       if (lane == 0) {
-        wsm[r] = s;
+        wsm[r] = cdf_split(s);
         hv2 += s.x * s.x + s.y * s.y;
       }
     }
@@ -309,14 +395,17 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(HayArgs A) {
     if (!grid_barrier(A.bar, A.status)) return;
     reduce_coeffs(A, A.h1, j + 1);
     if (!grid_barrier(A.bar, A.status)) return;
-    subtract_projection(A, wsm, red, A.h1, row0, nrows, j + 1);
+    subtract_projection(A, wsm, red, hs, A.h1, row0, nrows, j + 1);
     project_partial(A, wsm, row0, nrows, j + 1);
     if (!grid_barrier(A.bar, A.status)) return;
     reduce_coeffs(A, A.h2, j + 1);
     if (!grid_barrier(A.bar, A.status)) return;
-    subtract_projection(A, wsm, red, A.h2, row0, nrows, j + 1);
+    subtract_projection(A, wsm, red, hs, A.h2, row0, nrows, j + 1);
     double ww = 0.0;
-    for (int r = threadIdx.x; r < nrows; r += kThreads) ww += wsm[r].x * wsm[r].x + wsm[r].y * wsm[r].y;
+    for (int r = threadIdx.x; r < nrows; r += kThreads) {
+      const double2 w = cdf_val(wsm[r]);
+      ww += w.x * w.x + w.y * w.y;
+    }
     ww = block_sum(ww, red1);
     if (threadIdx.x == 0) A.npart[2 * blockIdx.x] = ww;
     if (!grid_barrier(A.bar, A.status)) return;
@@ -338,10 +427,11 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(HayArgs A) {
       break;
     }
     const double binv = 1.0 / bn;
-    double2* Vn = A.V + (size_t)(j + 1) * dim + row0;
+    float4* Vn = A.V + (size_t)(j + 1) * dim + row0;
     for (int r = threadIdx.x; r < nrows; r += kThreads) {
-      const double2 v = make_double2(wsm[r].x * binv, wsm[r].y * binv);
-      Vn[r] = v;
+      const double2 w = cdf_val(wsm[r]);
+      const double2 v = make_double2(w.x * binv, w.y * binv);
+      Vn[r] = cdf_split(v);
       A.vf[row0 + r] = make_float2((float)v.x, (float)v.y);
     }
     if (!grid_barrier(A.bar, A.status)) return;
@@ -407,7 +497,7 @@ size_t spectrum_ws_bytes(const DevSys& d, long long nsteps) { return spec_layout
 
 // Shared with the adjoint: runs the recursion into a caller-laid-out workspace.
 int run_haydock(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw, double eta,
-                double* eps2, double* ab, int* steps_done, void* ws, int* status, void* stream, double2** V_out) {
+                double* eps2, double* ab, int* steps_done, void* ws, int* status, void* stream, float4** V_out) {
   cudaStream_t st = (cudaStream_t)stream;
   const SpecLayout L = spec_layout(d, nsteps);
   char* base = (char*)ws;
@@ -415,7 +505,7 @@ int run_haydock(const DevSys& d, const void* H, const void* P, int nsteps, const
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int rows_per_max = (d.dim + sms - 1) / sms;
-  const size_t dyn = (size_t)rows_per_max * sizeof(double2);
+  const size_t dyn = ((size_t)rows_per_max + (size_t)nsteps) * sizeof(float4);
   if (dyn > 160 * 1024) return -1;
   cudaFuncSetAttribute((const void*)haydock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, haydock_kernel, kThreads, dyn);
@@ -433,7 +523,7 @@ int run_haydock(const DevSys& d, const void* H, const void* P, int nsteps, const
   A.eps2 = eps2;
   A.ab = ab;
   A.steps_done = steps_done;
-  A.V = (double2*)(base + L.V);
+  A.V = (float4*)(base + L.V);
   A.vf = (float2*)(base + L.vf);
   A.hpart = (double2*)(base + L.hpart);
   A.h1 = (double2*)(base + L.h1);

@@ -83,5 +83,5 @@ int launch_backward(const DevSys& d, const long long* h_qblk_off, const long lon
                     void* drho_dir, void* dW, void* ws, int* status, void* stream);
 int upload_twiddles();
 int run_haydock(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw, double eta,
-                double* eps2, double* ab, int* steps_done, void* ws, int* status, void* stream, double2** V_out);
+                double* eps2, double* ab, int* steps_done, void* ws, int* status, void* stream, float4** V_out);
 }  // namespace bse

@@ -115,8 +115,9 @@ struct PairCfg {
   static constexpr int LD = N3 + 2;    // z-line stride in shared memory: 16-B aligned rows, float4 reads conflict-free
   static constexpr int NCH = N1 * (N2 / ROWS);
   static_assert(N2 % ROWS == 0, "ROWS must divide N2");
+  static constexpr int S1P = (N2 + 1) * M3;   // product stride of S1 (one padding row: spreads banks)
   static size_t smem(int ng_max) {
-    return sizeof(float2) * ((size_t)2 * BMAX * ROWS * LD + (size_t)PMAX * N2 * M3 + (size_t)PMAX * M2 * M3) +
+    return sizeof(float2) * ((size_t)2 * BMAX * ROWS * LD + (size_t)PMAX * S1P + (size_t)PMAX * M2 * M3 + N1) +
            sizeof(int2) * (size_t)ng_max;
   }
 };
@@ -231,13 +232,14 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
                                                           float2* __restrict__ out, int mode, int q0, int nqc,
                                                           long long vbase) {
   using C = PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, ACC, THREADS, MERGED>;
-  constexpr int M2 = C::M2, M3 = C::M3, LD = C::LD, NCH = C::NCH;
+  constexpr int M2 = C::M2, M3 = C::M3, LD = C::LD, NCH = C::NCH, S1P = C::S1P;
   constexpr int CPR = N2 / ROWS;            // chunks per slab
   extern __shared__ float4 sm4[];
   float2* ub = reinterpret_cast<float2*>(sm4);   // [2][BMAX][ROWS][LD]
-  float2* S1 = ub + 2 * BMAX * ROWS * LD;         // [PMAX][N2][M3]
-  float2* S2 = S1 + PMAX * N2 * M3;               // [PMAX][M2][M3]
-  int2* sg = reinterpret_cast<int2*>(S2 + PMAX * M2 * M3);
+  float2* S1 = ub + 2 * BMAX * ROWS * LD;         // [PMAX][N2 (+1 pad)][M3]
+  float2* S2 = S1 + PMAX * S1P;                   // [PMAX][M2][M3]
+  float2* tw1 = S2 + PMAX * M2 * M3;              // [N1] exp(-2 pi i g j1/N1) of the current slab
+  int2* sg = reinterpret_cast<int2*>(tw1 + N1);
 
   Job jb;
   if (!decode_job(d, mode, MERGED, q0, nqc, vbase, out, jb)) return;
@@ -249,7 +251,7 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
   for (int t = tid; t < NG; t += THREADS) {
     const char4 g = d.gq[(size_t)jb.q * d.ng_max + t];
     const int G1 = g.x - jb.g0x, G2 = g.y - jb.g0y, G3 = g.z - jb.g0z;   // G = g_p - G0
-    sg[t] = make_int2(G1, (G2 + F2) * M3 + (G3 + F3));
+    sg[t] = make_int2(((G1 % N1) + N1) % N1, (G2 + F2) * M3 + (G3 + F3));
   }
   float2 acc[ACC];
 #pragma unroll
@@ -263,13 +265,15 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
   auto issue = [&](int c) {
     const int j1 = c / CPR, r0 = (c - j1 * CPR) * ROWS;
     float2* dstb = ub + (size_t)(c & 1) * BMAX * ROWS * LD;
-    constexpr int H = N3 / 2;               // 16-byte pieces per z-line
-    for (int idx = tid; idx < nbands * ROWS * H; idx += THREADS) {
-      const int bi = idx / (ROWS * H);
-      const int rem = idx - bi * (ROWS * H);
-      const int row = rem / H, h = rem - row * H;
-      const float2* src = (bi < jb.na) ? ua + (size_t)bi * vol : ubb + (size_t)(bi - jb.na) * vol;
-      cp_async16(dstb + ((size_t)bi * ROWS + row) * LD + 2 * h, src + ((size_t)j1 * N2 + r0 + row) * N3 + 2 * h);
+    constexpr int H = N3 / 2;               // 16-byte pieces per z-line; a chunk is ROWS contiguous lines
+    const size_t goff = ((size_t)j1 * N2 + r0) * N3;
+    for (int bi = 0; bi < nbands; ++bi) {
+      const float2* src = ((bi < jb.na) ? ua + (size_t)bi * vol : ubb + (size_t)(bi - jb.na) * vol) + goff;
+      float2* dst = dstb + (size_t)bi * ROWS * LD;
+      for (int e = tid; e < ROWS * H; e += THREADS) {
+        const int row = e / H, h = e - row * H;
+        cp_async16(dst + row * LD + 2 * h, src + 2 * e);
+      }
     }
     cp_async_commit();
   };
@@ -300,7 +304,7 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
         x[2 * h + 1] = make_float2(va.z * vb.z + va.w * vb.w, va.z * vb.w - va.w * vb.z);
       }
       fft::line<N3, true>(c_tw, x);
-      float2* s1 = S1 + ((size_t)p * N2 + r0 + row) * M3;
+      float2* s1 = S1 + (size_t)p * S1P + (size_t)(r0 + row) * M3;
 #pragma unroll
       for (int f = -F3; f <= F3; ++f) s1[f + F3] = x[(f + N3) % N3];
     }
@@ -310,11 +314,12 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
         const int p = it / M3, m3 = it - p * M3;
         float2 y[N2];
 #pragma unroll
-        for (int j = 0; j < N2; ++j) y[j] = S1[((size_t)p * N2 + j) * M3 + m3];
+        for (int j = 0; j < N2; ++j) y[j] = S1[(size_t)p * S1P + (size_t)j * M3 + m3];
         fft::line<N2, true>(c_tw, y);
 #pragma unroll
         for (int f = -F2; f <= F2; ++f) S2[((size_t)p * M2 + (f + F2)) * M3 + m3] = y[(f + N2) % N2];
       }
+      for (int g = tid; g < N1; g += THREADS) tw1[g] = fft::tw<N1, true>(c_tw, g * j1);
       __syncthreads();
 #pragma unroll
       for (int a = 0; a < ACC; ++a) {                            // stage 3: x DFT at sphere points
@@ -323,7 +328,7 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
           const int p = idx / NG, t = idx - p * NG;
           const int2 g = sg[t];
           const float2 s = S2[(size_t)p * M2 * M3 + g.y];
-          acc[a] = cadd(acc[a], cmul(s, fft::tw<N1, true>(c_tw, g.x * j1)));
+          acc[a] = cadd(acc[a], cmul(s, tw1[g.x]));
         }
       }
     }
