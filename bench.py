@@ -194,6 +194,58 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e_steps
 
+    # mixed precision: the same step with the BF16 hi/lo tensor-core contractions
+    mixed = None
+    if not args.no_mixed:
+        eps_fp32 = F.eps2.clone()
+        evm = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+        prec_save = prec
+        prec = bse.BSE_PREC_BF16X3
+
+        def step_mixed(record=None):
+            def mark(i):
+                if record is not None:
+                    record[i].record(stream)
+            mark(0)
+            bse.bse_pair_densities(plan, 0, bse.BSE_PD_REALSPACE | bse.BSE_PD_EXCHANGE, coef, en, F.rho_x, F.P, None,
+                                   0, 0, F.ws_pair)
+            mark(1)
+            bse.bse_build_kernel(plan, 0, bse.BSE_BK_INIT, F.rho_x, None, 0, 0, None, en, spec.delta, prec, F.H, None)
+            mark(2)
+            for q0, q1 in F.chunks:
+                bse.bse_pair_densities(plan, 0, bse.BSE_PD_DIRECT, None, None, None, None, F.rho_dir, q0, q1,
+                                       F.ws_pair)
+                mark(3)
+                bse.bse_build_kernel(plan, 0, bse.BSE_BK_DIRECT, None, F.rho_dir, q0, q1, W, None, spec.delta, prec,
+                                     F.H, F.ws_kernel)
+                mark(4)
+            bse.bse_spectrum(plan, 0, F.H, F.P, spec.nsteps, om, spec.eta, F.eps2, F.ab, F.steps_done, F.ws_spec)
+            mark(5)
+
+        for _ in range(args.warmup):
+            step_mixed()
+        torch.cuda.synchronize()
+        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        for k in range(args.steps):
+            step_mixed(evm[k])
+        m1.record(stream)
+        torch.cuda.synchronize()
+        bse.bse_status_read(plan)
+        prec = prec_save
+        ms_mixed = m0.elapsed_time(m1) / args.steps
+        st_mixed = {n: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evm) for i, n in enumerate(ev_names)}
+        err = float((F.eps2 - eps_fp32).abs().max() / eps_fp32.abs().max())
+        w_side = min(spec.nv ** 2, spec.nc ** 2)
+        ng = inf["ng_max"]
+        issued = 24.0 * inf["nblocks"] * w_side * ng * ng / len(F.chunks)     # 3 splits x 8 flops per complex MAC
+        mixed = {"prec": "bf16x3", "ms_per_step": ms_mixed, "value": world * dim * dim / (ms_mixed / 1e3),
+                 "stages_ms": st_mixed, "eps2_rel_err_vs_fp32": err,
+                 "direct_contract_speedup_vs_fp32": stage_ms["direct_contract"] / st_mixed["direct_contract"],
+                 "direct_contract_issued_bf16_tflops_upper_bound": issued / (st_mixed["direct_contract"] / 1e3) / 1e12}
+        step()       # restore the FP32 state
+        torch.cuda.synchronize()
+
     peaks, src = _peaks()
     # dominant stage: by measured time
     dom = max(stage_ms, key=stage_ms.get)
@@ -215,6 +267,7 @@ def run_ours(args):
         "e2e": {"value": world * dim * dim / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
+        "mixed": mixed,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(spec, s, budget_s=args.cpu_budget)
@@ -369,6 +422,7 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the BF16x3 comparison run")
     ap.add_argument("--only", default="all", choices=["all", "pair", "spectrum"],
                     help="profiling aid: run one stage (pair: realspace + a q chunk of pair densities; "
                          "spectrum: Haydock on an H built once before the loop)")

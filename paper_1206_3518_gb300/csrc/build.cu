@@ -191,14 +191,20 @@ int launch_gemm_wr(const DevSys& d, const void* rho_dir, int q_begin, int q_end,
 
 int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long b_begin,
                                long long b_count, long long vbase, long long max_rows, const void* W, int prec,
-                               void* H, void* ws, void* stream) {
-  if (prec != BSE_PREC_FP32) return -1;
+                               void* H, void* ws, int* status, void* stream) {
   const int side_c = (d.nc * d.nc < d.nv * d.nv) ? 1 : 0;
   cudaStream_t st = (cudaStream_t)stream;
-  dim3 grid((d.ng_max + BN - 1) / BN, (unsigned)((max_rows + BM - 1) / BM), q_end - q_begin);
-  gemm_wr<<<grid, kGemmThreads, 0, st>>>(d, (const float2*)rho_dir, (const float2*)W, (float2*)ws, q_begin, vbase,
-                                         side_c);
-  int e = (int)cudaGetLastError();
+  int e;
+  if (prec == BSE_PREC_BF16X3) {
+    e = launch_gemm_wr_tc(d, rho_dir, q_begin, q_end, vbase, max_rows, W, ws, side_c, status, stream);
+  } else if (prec == BSE_PREC_FP32) {
+    dim3 grid((d.ng_max + BN - 1) / BN, (unsigned)((max_rows + BM - 1) / BM), q_end - q_begin);
+    gemm_wr<<<grid, kGemmThreads, 0, st>>>(d, (const float2*)rho_dir, (const float2*)W, (float2*)ws, q_begin, vbase,
+                                           side_c);
+    e = (int)cudaGetLastError();
+  } else {
+    return -1;
+  }
   if (e) return e;
   if (b_count > 0)
     block_kernel<<<(unsigned)b_count, kBlkThreads, 0, st>>>(d, (const float2*)rho_dir, (const float2*)ws, (float2*)H,

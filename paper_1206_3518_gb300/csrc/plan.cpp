@@ -497,7 +497,8 @@ bse_status bse_build_kernel(bse_plan* plan, int s, unsigned flags, const void* r
     const long long w = (d.nc * d.nc < d.nv * d.nv) ? d.nc * d.nc : d.nv * d.nv;
     long long max_rows = 0;
     for (int q = q_begin; q < q_end; ++q) max_rows = std::max(max_rows, (sp.qblk_off[q + 1] - sp.qblk_off[q]) * w);
-    const int e = launch_kernel_direct_range(d, rho_dir, q_begin, q_end, b0, nb, vb, max_rows, W, prec, H, ws, stream);
+    const int e = launch_kernel_direct_range(d, rho_dir, q_begin, q_end, b0, nb, vb, max_rows, W, prec, H, ws,
+                                             plan->d_status, stream);
     if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "precision not available in this build");
     if ((st = cuda_check(e, "kernel direct")) != BSE_OK) return st;
   }
