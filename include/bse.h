@@ -216,6 +216,21 @@ bse_status bse_spectrum(bse_plan* plan, int s, const void* H, const void* P, int
                         void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * A7 + A8 for a batch of n <= 24 systems of one plan in ONE persistent cooperative
+ * launch: the grid (one CTA per SM) is split into per-system CTA groups sized by each
+ * system's H bytes (at least one CTA), each group runs the recursion of bse_spectrum on
+ * its system with group-local bounded barriers, so small and large systems progress
+ * together (the layered 2D batch of Sec. V-sized sheets).  Per-system arguments are host
+ * arrays of device pointers: H[i], P[i], eps2[i] [nw], ab[i] [2*nsteps], steps_done[i],
+ * ws[i] (bse_workspace_size(BSE_WS_SPECTRUM, nsteps) of that system, ws_bytes[i]).
+ * All systems share nsteps, omega (device, nw) and eta.
+ */
+bse_status bse_spectrum_batch(bse_plan* plan, int n, const int* systems, const void* const* H,
+                              const void* const* P, int nsteps, const double* omega, int nw, double eta,
+                              double* const* eps2, double* const* ab, int* const* steps_done,
+                              void* const* ws, const size_t* ws_bytes, void* stream);
+
+/*
  * bse_spectrum without a caller workspace.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc when they run the
  * spectrum - for example code behind a foreign-function boundary that is handed

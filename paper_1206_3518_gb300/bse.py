@@ -26,7 +26,7 @@ BSE_BK_INIT, BSE_BK_DIRECT = 1, 2
 EXPORTED = [
     "bse_last_error", "bse_plan_create", "bse_plan_create_host", "bse_plan_destroy", "bse_plan_info", "bse_gvectors",
     "bse_pair_blocks", "bse_workspace_size", "bse_rho_dir_count", "bse_pair_densities",
-    "bse_build_kernel", "bse_apply_H", "bse_spectrum", "bse_spectrum_static", "bse_spectrum_backward", "bse_status_read",
+    "bse_build_kernel", "bse_apply_H", "bse_spectrum", "bse_spectrum_static", "bse_spectrum_batch", "bse_spectrum_backward", "bse_status_read",
 ]
 
 
@@ -77,6 +77,9 @@ def load():
     lib.bse_apply_H.argtypes = [vp, i, vp, vp, vp, i, vp]
     lib.bse_spectrum.argtypes = [vp, i, vp, vp, i, vp, i, d, vp, vp, vp, vp, sz, vp]
     lib.bse_spectrum_static.argtypes = [vp, i, vp, vp, i, vp, i, d, vp, vp, vp, vp]
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    lib.bse_spectrum_batch.argtypes = [vp, i, ctypes.POINTER(i), pp, pp, i, vp, i, d, pp, pp, pp, pp,
+                                       ctypes.POINTER(sz), vp]
     lib.bse_spectrum_backward.argtypes = [vp, i, vp, vp, i, vp, i, d, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.bse_status_read.argtypes = [vp, vp]
     for name in EXPORTED:
@@ -214,6 +217,20 @@ def bse_spectrum(plan, s, H, P, nsteps, omega, eta, eps2, ab, steps_done, ws):
     _check(load().bse_spectrum(plan.handle, s, _ptr(H), _ptr(P), int(nsteps), _ptr(omega), omega.numel(),
                                float(eta), _ptr(eps2), _ptr(ab), _ptr(steps_done), _ptr(ws), _nbytes(ws),
                                _stream()))
+
+
+def bse_spectrum_batch(plan, systems, H, P, nsteps, omega, eta, eps2, ab, steps_done, ws):
+    """Per-system lists of device tensors; one cooperative launch for all systems."""
+    n = len(systems)
+
+    def arr(ts):
+        return (ctypes.c_void_p * n)(*[ctypes.c_void_p(t.data_ptr()) for t in ts])
+    for t in list(H) + list(P) + list(eps2) + list(ab) + list(steps_done) + list(ws):
+        _ptr(t)
+    sysa = (ctypes.c_int * n)(*systems)
+    wsb = (ctypes.c_size_t * n)(*[_nbytes(w) for w in ws])
+    _check(load().bse_spectrum_batch(plan.handle, n, sysa, arr(H), arr(P), int(nsteps), _ptr(omega), omega.numel(),
+                                     float(eta), arr(eps2), arr(ab), arr(steps_done), arr(ws), wsb, _stream()))
 
 
 def bse_spectrum_static(plan, s, H, P, nsteps, omega, eta, eps2, ab, steps_done):

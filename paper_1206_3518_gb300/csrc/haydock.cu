@@ -38,9 +38,9 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
-// Grid-wide barrier over a (count, generation) pair; false if the wait timed out or
-// another CTA already reported an error.
-__device__ bool grid_barrier(unsigned* bar, int* status) {
+// Barrier over the gsize CTAs of one system's group, on a (count, generation) pair; false if
+// the wait timed out or another CTA already reported an error.
+__device__ bool grid_barrier(unsigned* bar, int* status, unsigned gsize) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -49,7 +49,7 @@ __device__ bool grid_barrier(unsigned* bar, int* status) {
     __threadfence();
     const unsigned arrived = atomicAdd(bar, 1u);
     int good = 1;
-    if (arrived == gridDim.x - 1) {
+    if (arrived == gsize - 1) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
@@ -221,7 +221,10 @@ __device__ __forceinline__ double2 row_dot(const float2* __restrict__ Hr, const 
 }
 
 struct HayArgs {
-  DevSys d;
+  int dim;
+  double prefactor;
+  int cta0, ncta;   // this system's CTA group inside the launch
+  int grank, gsize; // filled per CTA: rank in the group, group size
   const float2* H;
   const double2* P;
   int nsteps;
@@ -244,7 +247,7 @@ struct HayArgs {
 // hpart[cta][i] = sum over own rows conj(V[i][r]) w[r], i in [0, n) (double-float products).
 __device__ void project_partial(const HayArgs& A, const float4* wsm, int row0, int nrows, int n) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int dim = A.d.dim;
+  const int dim = A.dim;
   for (int i = warp; i < n; i += kWarps) {
     const float4* Vi = A.V + (size_t)i * dim + row0;
     float2 sr = make_float2(0.f, 0.f), si = make_float2(0.f, 0.f);
@@ -259,16 +262,16 @@ __device__ void project_partial(const HayArgs& A, const float4* wsm, int row0, i
       df_mac(si, df_neg(vi), wr);
     }
     const float4 t = cdf_warp_sum(make_float4(sr.x, sr.y, si.x, si.y));
-    if (lane == 0) A.hpart[(size_t)blockIdx.x * A.nsteps + i] = cdf_val(t);
+    if (lane == 0) A.hpart[(size_t)A.grank * A.nsteps + i] = cdf_val(t);
   }
 }
 
 // h[i] = sum_cta hpart[cta][i] for the i owned by this CTA (deterministic order, FP64).
 __device__ void reduce_coeffs(const HayArgs& A, double2* h, int n) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = blockIdx.x + gridDim.x * warp; i < n; i += gridDim.x * kWarps) {
+  for (int i = A.grank + A.gsize * warp; i < n; i += A.gsize * kWarps) {
     double2 s = make_double2(0.0, 0.0);
-    for (int c = lane; c < (int)gridDim.x; c += 32) {
+    for (int c = lane; c < A.gsize; c += 32) {
       const double2 v = __ldcg(A.hpart + (size_t)c * A.nsteps + i);
       s.x += v.x;
       s.y += v.y;
@@ -282,7 +285,7 @@ __device__ void reduce_coeffs(const HayArgs& A, double2* h, int n) {
 __device__ void subtract_projection(const HayArgs& A, float4* wsm, float4 (*red)[32], float4* hs, const double2* h,
                                     int row0, int nrows, int n) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int dim = A.d.dim;
+  const int dim = A.dim;
   for (int i = threadIdx.x; i < n; i += kThreads) hs[i] = cdf_split(__ldcg(h + i));
   __syncthreads();
   for (int r0 = 0; r0 < nrows; r0 += 32) {
@@ -338,7 +341,7 @@ __device__ double block_sum(double v, double* red1) {
 // sum over CTAs of npart[c][which], identical order in every CTA.
 __device__ double all_cta_sum(const HayArgs& A, int which, double* red1) {
   double v = 0.0;
-  for (int c = threadIdx.x; c < (int)gridDim.x; c += kThreads) v += __ldcg(A.npart + 2 * c + which);
+  for (int c = threadIdx.x; c < A.gsize; c += kThreads) v += __ldcg(A.npart + 2 * c + which);
   double t = block_sum(v, red1);
   __shared__ double bc;
   if (threadIdx.x == 0) bc = t;
@@ -346,15 +349,70 @@ __device__ double all_cta_sum(const HayArgs& A, int which, double* red1) {
   return bc;
 }
 
-__global__ __launch_bounds__(kThreads, 1) void haydock_kernel(HayArgs A) {
+constexpr int kMaxBatch = 24;
+
+// One system of a batched launch (pointers into that system's workspace).
+struct HaySys {
+  int dim, cta0, ncta;
+  double prefactor;
+  const float2* H;
+  const double2* P;
+  double* eps2;
+  double* ab;
+  int* steps_done;
+  float4* V;
+  float2* vf;
+  double2* hpart;
+  double2* h1;
+  double2* h2;
+  double* npart;
+  unsigned* bar;
+};
+
+struct HayBatch {
+  int nsys, nsteps, nw, rows_max;   // rows_max: largest rows-per-CTA over the systems
+  double eta;
+  const double* omega;
+  int* status;
+  HaySys s[kMaxBatch];
+};
+
+__global__ __launch_bounds__(kThreads, 1) void haydock_kernel(const __grid_constant__ HayBatch B) {
+  int g = 0;
+  while (g + 1 < B.nsys && (int)blockIdx.x >= B.s[g + 1].cta0) ++g;
+  const HaySys& S = B.s[g];
+  HayArgs A;
+  A.dim = S.dim;
+  A.prefactor = S.prefactor;
+  A.cta0 = S.cta0;
+  A.ncta = S.ncta;
+  A.grank = (int)blockIdx.x - S.cta0;
+  A.gsize = S.ncta;
+  A.H = S.H;
+  A.P = S.P;
+  A.nsteps = B.nsteps;
+  A.omega = B.omega;
+  A.nw = B.nw;
+  A.eta = B.eta;
+  A.eps2 = S.eps2;
+  A.ab = S.ab;
+  A.steps_done = S.steps_done;
+  A.V = S.V;
+  A.vf = S.vf;
+  A.hpart = S.hpart;
+  A.h1 = S.h1;
+  A.h2 = S.h2;
+  A.npart = S.npart;
+  A.bar = S.bar;
+  A.status = B.status;
   extern __shared__ float4 dyn[];
   float4* wsm = dyn;                                // own rows of w (double-float)
-  float4* hs = dyn + ((A.d.dim + gridDim.x - 1) / gridDim.x);   // projection coefficients (double-float)
+  float4* hs = dyn + B.rows_max;                    // projection coefficients (double-float)
   __shared__ float4 red[kWarps][32];
   __shared__ double red1[kWarps];
-  const int dim = A.d.dim;
-  const int rows_per = (dim + gridDim.x - 1) / gridDim.x;
-  const int row0 = min(dim, (int)blockIdx.x * rows_per);
+  const int dim = A.dim;
+  const int rows_per = (dim + A.gsize - 1) / A.gsize;
+  const int row0 = min(dim, A.grank * rows_per);
   const int nrows = min(dim, row0 + rows_per) - row0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -365,8 +423,8 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(HayArgs A) {
     pp += p.x * p.x + p.y * p.y;
   }
   pp = block_sum(pp, red1);
-  if (threadIdx.x == 0) A.npart[2 * blockIdx.x] = pp;
-  if (!grid_barrier(A.bar, A.status)) return;
+  if (threadIdx.x == 0) A.npart[2 * A.grank] = pp;
+  if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
   const double pn2 = all_cta_sum(A, 0, red1);
   const double pinv = 1.0 / sqrt(pn2);
   for (int r = threadIdx.x; r < nrows; r += kThreads) {
@@ -375,7 +433,7 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(HayArgs A) {
     A.V[row0 + r] = cdf_split(v);
     A.vf[row0 + r] = make_float2((float)v.x, (float)v.y);
   }
-  if (!grid_barrier(A.bar, A.status)) return;
+  if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
 
   int done = A.nsteps;
   for (int j = 0; j < A.nsteps; ++j) {
@@ -389,17 +447,17 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(HayArgs A) {
       }
     }
     hv2 = block_sum(hv2, red1);
-    if (threadIdx.x == 0) A.npart[2 * blockIdx.x + 1] = hv2;
+    if (threadIdx.x == 0) A.npart[2 * A.grank + 1] = hv2;
     __syncthreads();
     project_partial(A, wsm, row0, nrows, j + 1);
-    if (!grid_barrier(A.bar, A.status)) return;
+    if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
     reduce_coeffs(A, A.h1, j + 1);
-    if (!grid_barrier(A.bar, A.status)) return;
+    if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
     subtract_projection(A, wsm, red, hs, A.h1, row0, nrows, j + 1);
     project_partial(A, wsm, row0, nrows, j + 1);
-    if (!grid_barrier(A.bar, A.status)) return;
+    if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
     reduce_coeffs(A, A.h2, j + 1);
-    if (!grid_barrier(A.bar, A.status)) return;
+    if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
     subtract_projection(A, wsm, red, hs, A.h2, row0, nrows, j + 1);
     double ww = 0.0;
     for (int r = threadIdx.x; r < nrows; r += kThreads) {
@@ -407,8 +465,8 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(HayArgs A) {
       ww += w.x * w.x + w.y * w.y;
     }
     ww = block_sum(ww, red1);
-    if (threadIdx.x == 0) A.npart[2 * blockIdx.x] = ww;
-    if (!grid_barrier(A.bar, A.status)) return;
+    if (threadIdx.x == 0) A.npart[2 * A.grank] = ww;
+    if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
     const double bn2 = all_cta_sum(A, 0, red1);
     const double sc2 = all_cta_sum(A, 1, red1);
     const double2 c1 = __ldcg(A.h1 + j), c2 = __ldcg(A.h2 + j);
@@ -416,7 +474,7 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(HayArgs A) {
     const double bn = sqrt(bn2);
     const bool last = (j + 1 == A.nsteps);
     const bool brk = !last && !(bn > kBreakdownRel * sqrt(sc2));
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (A.grank == 0 && threadIdx.x == 0) {
       A.ab[j] = aj;
       if (j == 0) A.ab[A.nsteps] = 0.0;
       if (!last) A.ab[A.nsteps + j + 1] = brk ? 0.0 : bn;
@@ -434,13 +492,13 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(HayArgs A) {
       Vn[r] = cdf_split(v);
       A.vf[row0 + r] = make_float2((float)v.x, (float)v.y);
     }
-    if (!grid_barrier(A.bar, A.status)) return;
+    if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
   }
-  if (!grid_barrier(A.bar, A.status)) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *A.steps_done = done;
+  if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
+  if (A.grank == 0 && threadIdx.x == 0) *A.steps_done = done;
   // continued fraction from the bottom: g = 1/(z - a_j - b_{j+1}^2 g)
-  const double C = A.d.prefactor * pn2;
-  for (int wi = blockIdx.x * kThreads + threadIdx.x; wi < A.nw; wi += gridDim.x * kThreads) {
+  const double C = A.prefactor * pn2;
+  for (int wi = A.grank * kThreads + threadIdx.x; wi < A.nw; wi += A.gsize * kThreads) {
     const double zr = A.omega[wi], zi = A.eta;
     double gr = 0.0, gi = 0.0;
     for (int jj = done - 1; jj >= 0; --jj) {
@@ -495,48 +553,79 @@ SpecLayout spec_layout(const DevSys& d, long long nsteps) {
 
 size_t spectrum_ws_bytes(const DevSys& d, long long nsteps) { return spec_layout(d, nsteps).total; }
 
-// Shared with the adjoint: runs the recursion into a caller-laid-out workspace.
-int run_haydock(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw, double eta,
-                double* eps2, double* ab, int* steps_done, void* ws, int* status, void* stream, float4** V_out) {
+// Launch the recursion for n systems in one cooperative grid of one CTA per SM; each system
+// gets a CTA group sized by its H bytes (at least one CTA) and its own workspace.
+int run_haydock_batch(const HayJob* jobs, int n, int nsteps, const double* omega, int nw, double eta, int* status,
+                      void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
-  const SpecLayout L = spec_layout(d, nsteps);
-  char* base = (char*)ws;
+  if (n < 1 || n > kMaxBatch) return -2;
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int rows_per_max = (d.dim + sms - 1) / sms;
-  const size_t dyn = ((size_t)rows_per_max + (size_t)nsteps) * sizeof(float4);
+  int grid = sms < kMaxGrid ? sms : kMaxGrid;
+  if (n > grid) return -2;
+  double tot = 0.0;
+  for (int i = 0; i < n; ++i) tot += (double)jobs[i].d->dim * jobs[i].d->dim;
+  int ncta[kMaxBatch];
+  int used = 0, big = 0;
+  for (int i = 0; i < n; ++i) {
+    const double share = (double)jobs[i].d->dim * jobs[i].d->dim / tot;
+    ncta[i] = 1 + (int)(share * (grid - n));
+    used += ncta[i];
+    if (jobs[i].d->dim > jobs[big].d->dim) big = i;
+  }
+  ncta[big] += grid - used;
+  HayBatch B;
+  B.nsys = n;
+  B.nsteps = nsteps;
+  B.nw = nw;
+  B.eta = eta;
+  B.omega = omega;
+  B.status = status;
+  B.rows_max = 0;
+  int cta = 0;
+  for (int i = 0; i < n; ++i) {
+    const DevSys& d = *jobs[i].d;
+    const SpecLayout L = spec_layout(d, nsteps);
+    char* base = (char*)jobs[i].ws;
+    HaySys& S = B.s[i];
+    S.dim = d.dim;
+    S.prefactor = d.prefactor;
+    S.cta0 = cta;
+    S.ncta = ncta[i];
+    cta += ncta[i];
+    S.H = (const float2*)jobs[i].H;
+    S.P = (const double2*)jobs[i].P;
+    S.eps2 = jobs[i].eps2;
+    S.ab = jobs[i].ab;
+    S.steps_done = jobs[i].steps_done;
+    S.V = (float4*)(base + L.V);
+    S.vf = (float2*)(base + L.vf);
+    S.hpart = (double2*)(base + L.hpart);
+    S.h1 = (double2*)(base + L.h1);
+    S.h2 = (double2*)(base + L.h2);
+    S.npart = (double*)(base + L.npart);
+    S.bar = (unsigned*)(base + L.bar);
+    const int rows = (d.dim + ncta[i] - 1) / ncta[i];
+    if (rows > B.rows_max) B.rows_max = rows;
+    const int e = (int)cudaMemsetAsync(S.bar, 0, 2 * sizeof(unsigned), st);
+    if (e) return e;
+  }
+  const size_t dyn = ((size_t)B.rows_max + (size_t)nsteps) * sizeof(float4);
   if (dyn > 160 * 1024) return -1;
   cudaFuncSetAttribute((const void*)haydock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, haydock_kernel, kThreads, dyn);
   if (occ < 1) return -1;
-  int grid = sms;                       // one CTA per SM: every CTA streams its own rows of H
-  if (grid > kMaxGrid) grid = kMaxGrid;
-  HayArgs A;
-  A.d = d;
-  A.H = (const float2*)H;
-  A.P = (const double2*)P;
-  A.nsteps = nsteps;
-  A.omega = omega;
-  A.nw = nw;
-  A.eta = eta;
-  A.eps2 = eps2;
-  A.ab = ab;
-  A.steps_done = steps_done;
-  A.V = (float4*)(base + L.V);
-  A.vf = (float2*)(base + L.vf);
-  A.hpart = (double2*)(base + L.hpart);
-  A.h1 = (double2*)(base + L.h1);
-  A.h2 = (double2*)(base + L.h2);
-  A.npart = (double*)(base + L.npart);
-  A.bar = (unsigned*)(base + L.bar);
-  A.status = status;
-  if (V_out) *V_out = A.V;
-  int e = (int)cudaMemsetAsync(A.bar, 0, 2 * sizeof(unsigned), st);
-  if (e) return e;
-  void* args[] = {&A};
-  e = (int)cudaLaunchCooperativeKernel((const void*)haydock_kernel, dim3(grid), dim3(kThreads), args, dyn, st);
-  return e;
+  void* args[] = {&B};
+  return (int)cudaLaunchCooperativeKernel((const void*)haydock_kernel, dim3(grid), dim3(kThreads), args, dyn, st);
+}
+
+// Shared with the adjoint: one system into a caller-laid-out workspace.
+int run_haydock(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw, double eta,
+                double* eps2, double* ab, int* steps_done, void* ws, int* status, void* stream, float4** V_out) {
+  HayJob j{&d, H, P, eps2, ab, steps_done, ws};
+  if (V_out) *V_out = (float4*)((char*)ws + spec_layout(d, nsteps).V);
+  return run_haydock_batch(&j, 1, nsteps, omega, nw, eta, status, stream);
 }
 
 int launch_spectrum(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw,

@@ -84,6 +84,17 @@ int launch_backward(const DevSys& d, const long long* h_qblk_off, const long lon
                     const void* rho_x, const void* rho_dir, const void* W, double* d_delta, void* dH, void* drho_x,
                     void* drho_dir, void* dW, void* ws, int* status, void* stream);
 int upload_twiddles();
+struct HayJob {
+  const DevSys* d;
+  const void* H;
+  const void* P;
+  double* eps2;
+  double* ab;
+  int* steps_done;
+  void* ws;
+};
+int run_haydock_batch(const HayJob* jobs, int n, int nsteps, const double* omega, int nw, double eta, int* status,
+                      void* stream);
 int run_haydock(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw, double eta,
                 double* eps2, double* ab, int* steps_done, void* ws, int* status, void* stream, float4** V_out);
 }  // namespace bse

@@ -527,6 +527,32 @@ bse_status bse_spectrum(bse_plan* plan, int s, const void* H, const void* P, int
   return cuda_check(e, "spectrum");
 }
 
+bse_status bse_spectrum_batch(bse_plan* plan, int n, const int* systems, const void* const* H,
+                              const void* const* P, int nsteps, const double* omega, int nw, double eta,
+                              double* const* eps2, double* const* ab, int* const* steps_done, void* const* ws,
+                              const size_t* ws_bytes, void* stream) {
+  if (!plan || !plan->d_status) return set_error(BSE_ERR_ARG, "plan is NULL or host-only");
+  if (n < 1 || n > 24 || !systems || !H || !P || !eps2 || !ab || !steps_done || !ws || !ws_bytes || !omega ||
+      nsteps < 1 || nw < 0 || !(eta > 0.0))
+    return set_error(BSE_ERR_ARG, "batch needs 1..24 systems, all per-system arrays, nsteps >= 1, eta > 0");
+  std::vector<HayJob> jobs(n);
+  for (int i = 0; i < n; ++i) {
+    const int s = systems[i];
+    bse_status st = check_device_plan(plan, s);
+    if (st != BSE_OK) return st;
+    const DevSys& d = plan->sys[s].d;
+    if (!H[i] || !P[i] || !eps2[i] || !ab[i] || !steps_done[i] || !ws[i])
+      return set_error(BSE_ERR_ARG, "NULL pointer in a batch entry");
+    if (nsteps > d.dim) return set_error(BSE_ERR_ARG, "nsteps > dim of a batched system");
+    if (ws_bytes[i] < spectrum_ws_bytes(d, nsteps)) return set_error(BSE_ERR_WORKSPACE, "batch workspace too small");
+    jobs[i] = HayJob{&d, H[i], P[i], eps2[i], ab[i], steps_done[i], ws[i]};
+  }
+  const int e = run_haydock_batch(jobs.data(), n, nsteps, omega, nw, eta, plan->d_status, stream);
+  if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "cooperative launch not possible on this device");
+  if (e == -2) return set_error(BSE_ERR_ARG, "more batched systems than SMs");
+  return cuda_check(e, "spectrum batch");
+}
+
 bse_status bse_spectrum_static(bse_plan* plan, int s, const void* H, const void* P, int nsteps, const double* omega,
                                int nw, double eta, double* eps2, double* ab, int* steps_done, void* stream) {
   bse_status st = check_device_plan(plan, s);

@@ -64,3 +64,23 @@ class Forward:
         bse.bse_spectrum(self.plan, self.s, self.H, self.P, n, omega, eta, self.eps2[: omega.numel()], self.ab,
                          self.steps_done, self.ws_spec)
         return self.eps2[: omega.numel()]
+
+
+class Batch:
+    """Several systems of one plan: per-system builds (q-streamed) and one batched spectrum launch."""
+
+    def __init__(self, plan: bse.Plan, nsteps: int, nw: int, qchunk: int = 64, device="cuda"):
+        self.plan, self.nsteps = plan, nsteps
+        self.sys = [Forward(plan, s, nsteps=nsteps, nw=nw, qchunk=min(qchunk, plan.info(s)["nq"]), device=device)
+                    for s in range(plan.nsys)]
+
+    def build(self, coefs, energies, Ws, deltas, prec=bse.BSE_PREC_FP32):
+        for F, c, e, w, dl in zip(self.sys, coefs, energies, Ws, deltas):
+            F.build(c, e, w, dl, prec)
+
+    def spectrum(self, omega, eta):
+        S = self.sys
+        bse.bse_spectrum_batch(self.plan, list(range(len(S))), [F.H for F in S], [F.P for F in S], self.nsteps,
+                               omega, eta, [F.eps2[: omega.numel()] for F in S], [F.ab for F in S],
+                               [F.steps_done for F in S], [F.ws_spec for F in S])
+        return [F.eps2[: omega.numel()] for F in S]

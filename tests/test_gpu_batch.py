@@ -1,0 +1,127 @@
+"""Batched systems: per-system builds and one persistent cooperative spectrum launch for all.
+
+Layered 2D workload: 16 hexagonal sheets (a = 4.7, c = 30 bohr, slab-truncated Coulomb) on
+k meshes 24x24..48x48 with 1-3 valence and conduction bands (dims 576..20736), four with a
+Dirac-like band pair.
+"""
+import numpy as np
+import pytest
+
+from oracle import kernel as ok
+from oracle import pair as op
+from oracle import spectrum as osp
+from synth import generate, slab_batch_specs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bse():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1206_3518_gb300 import bse as b
+    return b
+
+
+def _dev(x, dtype):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+def _batch(bse, systems, nsteps, nw, qchunk=64):
+    from paper_1206_3518_gb300.pipeline import Batch
+    plan = bse.Plan([s.spec for s in systems])
+    B = Batch(plan, nsteps, nw, qchunk=qchunk)
+    ins = ([_dev(s.coef, torch.complex64) for s in systems], [_dev(s.energies, torch.float64) for s in systems],
+           [_dev(s.W, torch.complex64) for s in systems], [s.spec.delta for s in systems])
+    return plan, B, ins
+
+
+def test_small_sheet_batch_full_parity(bse):
+    specs = [sp.replace(name=f"small{i}", nk=(n, n, 1), nsteps=24, nw=300)
+             for i, (sp, n) in enumerate(zip(slab_batch_specs(0)[:6], (5, 6, 7, 8, 9, 6)))]
+    systems = [generate(sp) for sp in specs]
+    plan, B, ins = _batch(bse, systems, 24, 300)
+    B.build(*ins)
+    om = _dev(systems[0].omega, torch.float64)
+    eps = [e.cpu().numpy() for e in B.spectrum(om, specs[0].eta)]
+    bse.bse_status_read(plan)
+    for s, e in zip(systems, eps):
+        spec = s.spec
+        rx = op.exchange_rho(spec, s.gk, s.coef)
+        fac = ok.direct_factors(spec, s.gk, s.coef)
+        H = ok.hamiltonian_from_factors(spec, s.energies, spec.delta, rx, fac, s.W)
+        P = op.dipole(spec, s.gk, s.coef, s.energies)
+        ref = osp.eps2_haydock(spec, H, P, s.omega, spec.eta, 24)[0]
+        # floor set by storing H in FP32 (derived from the oracle alone, eta = 0.05 eV here); the GPU's
+        # H entries carry a few FP32 roundings each (kernel sums), hence 10x that floor
+        r32 = osp.eps2_haydock(spec, H.astype(np.complex64).astype(np.complex128), P, s.omega, spec.eta, 24)[0]
+        floor = np.abs(r32 - ref).max() / ref.max()
+        assert np.abs(e - ref).max() / ref.max() < max(1e-5, 10.0 * floor)
+
+
+def test_layered_2d_batch_of_16_sheets(bse):
+    specs = slab_batch_specs(0)
+    systems = [generate(sp, wdtype=np.complex64) for sp in specs]
+    nsteps, nw = 300, 2000
+    plan, B, ins = _batch(bse, systems, nsteps, nw)
+    om = _dev(systems[0].omega, torch.float64)
+    eta = specs[0].eta
+    B.build(*ins)
+    eps = [e.clone() for e in B.spectrum(om, eta)]
+    bse.bse_status_read(plan)
+    # each batched recursion matches the single-system launch; the CTA groups differ, so the
+    # reductions round differently and 300 Lanczos steps amplify that to ~1e-6
+    for F, e in zip(B.sys, eps):
+        assert int(F.steps_done.item()) == nsteps
+        single = F.spectrum(om, eta).clone()
+        assert float((single - e).abs().max() / single.abs().max()) < 1e-5
+    bse.bse_status_read(plan)
+    # sampled H blocks of the smallest and the largest sheet against the oracle
+    dims = [sp.dim for sp in specs]
+    for i in (int(np.argmin(dims)), int(np.argmax(dims))):
+        s, F = systems[i], B.sys[i]
+        spec = s.spec
+        nvc = spec.nv * spec.nc
+        rng = np.random.default_rng(i)
+        g0 = op.geo.sphere(spec, (0, 0, 0))
+        for ik, ik2 in [(0, 0)] + [tuple(sorted(rng.integers(0, spec.nkpt, 2))) for _ in range(4)]:
+            if ik == ik2 and nvc == 1:
+                continue                      # a 1x1 diagonal block holds only the transition energy
+            rx = op.rho_corr(spec, ik, ik, list(range(spec.nv)), list(range(spec.nv, spec.nb)), g0, s.gk,
+                             s.coef).reshape(nvc, -1)
+            rx2 = op.rho_corr(spec, ik2, ik2, list(range(spec.nv)), list(range(spec.nv, spec.nb)), g0, s.gk,
+                              s.coef).reshape(nvc, -1)
+            kx = ok.norm_factor(spec) * (np.conj(rx) * ok.coulomb_bar(spec)[None, :]) @ rx2.T
+            iq, rv, rc = op.direct_rho_block(spec, ik, ik2, s.gk, s.coef)
+            ref = 2.0 * kx - ok.direct_block(spec, rv, rc, ok.w_of_q(spec, s.W, iq))
+            got = F.H[ik * nvc:(ik + 1) * nvc, ik2 * nvc:(ik2 + 1) * nvc].cpu().numpy()
+            off = ~np.eye(nvc, dtype=bool) if ik == ik2 else np.ones((nvc, nvc), bool)
+            if ik == ik2:
+                ref = 0.5 * (ref + ref.conj().T)
+            assert np.abs(got - ref)[off].max() / np.abs(ref[off]).max() < 1e-5
+
+
+def test_batch_graph_capture_replays_identically(bse):
+    """The whole sequence (pair densities, kernels, batched spectrum) captured in one CUDA graph."""
+    specs = [sp.replace(name=f"g{i}", nk=(n, n, 1), nsteps=24, nw=300)
+             for i, (sp, n) in enumerate(zip(slab_batch_specs(0)[:4], (6, 8, 5, 7)))]
+    systems = [generate(sp) for sp in specs]
+    plan, B, ins = _batch(bse, systems, 24, 300)
+    om = _dev(systems[0].omega, torch.float64)
+    B.build(*ins)
+    eager = [e.clone() for e in B.spectrum(om, specs[0].eta)]
+    torch.cuda.synchronize()
+    for F in B.sys:
+        F.eps2.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        B.build(*ins)
+        B.spectrum(om, specs[0].eta)
+    g.replay()
+    torch.cuda.synchronize()
+    bse.bse_status_read(plan)
+    for F, e in zip(B.sys, eager):
+        assert torch.equal(F.eps2[:300], e)
