@@ -288,22 +288,29 @@ def run_stage(args):
 
     spec, s = make_inputs(args.config)
     plan = bse.Plan([spec])
-    qchunk = args.qchunk or (16 if args.only == "pair" else 32)
+    qchunk = args.qchunk or (16 if args.only in ("pair", "contract") else 32)
     F = Forward(plan, 0, nsteps=spec.nsteps, nw=spec.nw, qchunk=qchunk)
     dev = torch.device("cuda")
     coef = torch.as_tensor(s.coef.astype(np.complex64), device=dev)
     en = torch.as_tensor(s.energies, device=dev)
     om = torch.as_tensor(s.omega, device=dev)
+    W = torch.as_tensor(s.W, device=dev)
     if args.only == "spectrum":
-        W = torch.as_tensor(s.W, device=dev)
         F.build(coef, en, W, spec.delta)
     bse.bse_pair_densities(plan, 0, bse.BSE_PD_REALSPACE | bse.BSE_PD_EXCHANGE, coef, en, F.rho_x, F.P, None, 0, 0,
                            F.ws_pair)
     q0, q1 = F.chunks[min(1, len(F.chunks) - 1)]
+    prec = bse.BSE_PREC_BF16X3 if args.prec == "bf16x3" else bse.BSE_PREC_FP32
+    if args.only == "contract":
+        bse.bse_pair_densities(plan, 0, bse.BSE_PD_DIRECT, None, None, None, None, F.rho_dir, q0, q1, F.ws_pair)
+        bse.bse_build_kernel(plan, 0, bse.BSE_BK_INIT, F.rho_x, None, 0, 0, None, en, spec.delta, prec, F.H, None)
 
     def once():
         if args.only == "pair":
             bse.bse_pair_densities(plan, 0, bse.BSE_PD_DIRECT, None, None, None, None, F.rho_dir, q0, q1, F.ws_pair)
+        elif args.only == "contract":
+            bse.bse_build_kernel(plan, 0, bse.BSE_BK_DIRECT, None, F.rho_dir, q0, q1, W, None, spec.delta, prec, F.H,
+                                 F.ws_kernel)
         else:
             F.spectrum(om, spec.eta)
 
@@ -319,7 +326,7 @@ def run_stage(args):
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
     bse.bse_status_read(plan)
-    nblk = sum(len(bse.bse_pair_blocks(plan, 0, q)[0]) for q in range(q0, q1)) if args.only == "pair" else 0
+    nblk = sum(len(bse.bse_pair_blocks(plan, 0, q)[0]) for q in range(q0, q1)) if args.only != "spectrum" else 0
     print(json.dumps({"stage": args.only, "config": spec.name, "ms": times, "q_range": [q0, q1], "blocks": nblk}))
 
 
@@ -423,7 +430,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the BF16x3 comparison run")
-    ap.add_argument("--only", default="all", choices=["all", "pair", "spectrum"],
+    ap.add_argument("--only", default="all", choices=["all", "pair", "spectrum", "contract"],
                     help="profiling aid: run one stage (pair: realspace + a q chunk of pair densities; "
                          "spectrum: Haydock on an H built once before the loop)")
     ap.add_argument("--qchunk", type=int, default=0, help="q points per direct-term chunk (0 = all)")

@@ -167,12 +167,15 @@ __global__ __launch_bounds__(kBlkThreads) void block_kernel(DevSys d, const floa
 
 }  // namespace
 
-size_t kernel_ws_bytes(const DevSys& d, long long qchunk) {
+// FP32 W.rho rows of a q chunk, then (for BSE_PREC_BF16X3) the split BF16 tile images.
+static size_t x_bytes(const DevSys& d, long long qchunk) {
   const long long w = (d.nv * d.nv <= d.nc * d.nc) ? d.nv * d.nv : d.nc * d.nc;
   long long nb = qchunk * d.nkpt;
   if (nb > d.nblocks) nb = d.nblocks;
-  return (size_t)(nb * w) * d.ng_max * sizeof(float2);
+  return (((size_t)(nb * w) * d.ng_max * sizeof(float2)) + 255) & ~(size_t)255;
 }
+
+size_t kernel_ws_bytes(const DevSys& d, long long qchunk) { return x_bytes(d, qchunk) + tc_split_bytes(d, qchunk); }
 
 int launch_kernel_init(const DevSys& d, const void* rho_x, const double* energies, double delta, void* H,
                        void* stream) {
@@ -196,7 +199,8 @@ int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin
   cudaStream_t st = (cudaStream_t)stream;
   int e;
   if (prec == BSE_PREC_BF16X3) {
-    e = launch_gemm_wr_tc(d, rho_dir, q_begin, q_end, vbase, max_rows, W, ws, side_c, status, stream);
+    void* split_ws = (char*)ws + x_bytes(d, q_end - q_begin);
+    e = launch_gemm_wr_tc(d, rho_dir, q_begin, q_end, vbase, max_rows, W, ws, split_ws, side_c, status, stream);
   } else if (prec == BSE_PREC_FP32) {
     dim3 grid((d.ng_max + BN - 1) / BN, (unsigned)((max_rows + BM - 1) / BM), q_end - q_begin);
     gemm_wr<<<grid, kGemmThreads, 0, st>>>(d, (const float2*)rho_dir, (const float2*)W, (float2*)ws, q_begin, vbase,

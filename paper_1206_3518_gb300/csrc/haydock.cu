@@ -31,6 +31,7 @@ namespace {
 constexpr int kThreads = 512, kWarps = kThreads / 32;
 constexpr int kMaxGrid = 1024;
 constexpr double kBreakdownRel = 1e-10;
+constexpr int kXTile = 8192;          // columns of v_j staged in shared memory per pass (64 KB)
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -218,6 +219,74 @@ __device__ __forceinline__ double2 row_dot(const float2* __restrict__ Hr, const 
   }
   const float4 t = cdf_warp_sum(make_float4(ar.x, ar.y, ai.x, ai.y));
   return cdf_val(t);
+}
+
+// Segment dot over cols columns starting at Hr (row pointer already offset), x in shared memory.
+// Returns the lane's compensated (re, im) partial (not warp-reduced).
+__device__ __forceinline__ void seg_dot(const float2* __restrict__ Hr, const float2* xs, int cols, int lane,
+                                        float2& ar, float2& ai) {
+  auto carry = [&](float2 s) {
+    df_add(ar, make_float2(s.x, 0.f));
+    df_add(ai, make_float2(s.y, 0.f));
+  };
+  if ((reinterpret_cast<uintptr_t>(Hr) & 15) == 0) {      // float4 pairs, odd tail by lane 0
+    const float4* h4 = reinterpret_cast<const float4*>(Hr);
+    const float4* x4 = reinterpret_cast<const float4*>(xs);
+    const int n4 = cols >> 1;
+    int i = lane;
+    for (; i + 32 * 15 < n4; i += 32 * 16) {
+      float4 h[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) h[u] = __ldcs(h4 + i + 32 * u);
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const float4 v = x4[i + 32 * u];
+        s.x = fmaf(h[u].x, v.x, fmaf(-h[u].y, v.y, s.x));
+        s.y = fmaf(h[u].x, v.y, fmaf(h[u].y, v.x, s.y));
+        s.x = fmaf(h[u].z, v.z, fmaf(-h[u].w, v.w, s.x));
+        s.y = fmaf(h[u].z, v.w, fmaf(h[u].w, v.z, s.y));
+        if ((u & 7) == 7) {
+          carry(s);
+          s = make_float2(0.f, 0.f);
+        }
+      }
+    }
+    float2 s = make_float2(0.f, 0.f);
+    int cnt = 0;
+    for (; i < n4; i += 32) {
+      const float4 h = __ldcs(h4 + i);
+      const float4 v = x4[i];
+      s.x = fmaf(h.x, v.x, fmaf(-h.y, v.y, s.x));
+      s.y = fmaf(h.x, v.y, fmaf(h.y, v.x, s.y));
+      s.x = fmaf(h.z, v.z, fmaf(-h.w, v.w, s.x));
+      s.y = fmaf(h.z, v.w, fmaf(h.w, v.z, s.y));
+      if (++cnt == 8) {
+        carry(s);
+        s = make_float2(0.f, 0.f);
+        cnt = 0;
+      }
+    }
+    carry(s);
+    if ((cols & 1) && lane == 0) {          // odd tail element
+      const float2 h = __ldcs(Hr + cols - 1), v = xs[cols - 1];
+      carry(make_float2(h.x * v.x - h.y * v.y, h.x * v.y + h.y * v.x));
+    }
+  } else {
+    float2 s = make_float2(0.f, 0.f);
+    int cnt = 0;
+    for (int i = lane; i < cols; i += 32) {
+      const float2 h = __ldcs(Hr + i), v = xs[i];
+      s.x = fmaf(h.x, v.x, fmaf(-h.y, v.y, s.x));
+      s.y = fmaf(h.x, v.y, fmaf(h.y, v.x, s.y));
+      if (++cnt == 16) {
+        carry(s);
+        s = make_float2(0.f, 0.f);
+        cnt = 0;
+      }
+    }
+    carry(s);
+  }
 }
 
 struct HayArgs {
@@ -408,6 +477,7 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(const __grid_const
   extern __shared__ float4 dyn[];
   float4* wsm = dyn;                                // own rows of w (double-float)
   float4* hs = dyn + B.rows_max;                    // projection coefficients (double-float)
+  float2* xs = reinterpret_cast<float2*>(hs + B.nsteps);   // column tile of v_j (FP32)
   __shared__ float4 red[kWarps][32];
   __shared__ double red1[kWarps];
   const int dim = A.dim;
@@ -437,14 +507,33 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(const __grid_const
 
   int done = A.nsteps;
   for (int j = 0; j < A.nsteps; ++j) {
-    // w = H v_j on own rows, |H v_j|^2 partial
-    double hv2 = 0.0;
-    for (int r = warp; r < nrows; r += kWarps) {
-      const double2 s = row_dot(A.H + (size_t)(row0 + r) * dim, A.vf, dim, lane);
-      if (lane == 0) {
-        wsm[r] = cdf_split(s);
-        hv2 += s.x * s.x + s.y * s.y;
+    // w = H v_j on own rows: v_j staged in shared memory in column tiles, H streamed once
+    for (int r = threadIdx.x; r < nrows; r += kThreads) wsm[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int col0 = 0; col0 < dim; col0 += kXTile) {
+      const int cols = min(kXTile, dim - col0);
+      __syncthreads();
+      for (int c = threadIdx.x; c < cols; c += kThreads) xs[c] = __ldcg(A.vf + col0 + c);
+      __syncthreads();
+      for (int r = warp; r < nrows; r += kWarps) {
+        float2 ar = make_float2(0.f, 0.f), ai = make_float2(0.f, 0.f);
+        seg_dot(A.H + (size_t)(row0 + r) * dim + col0, xs, cols, lane, ar, ai);
+        const float4 t = cdf_warp_sum(make_float4(ar.x, ar.y, ai.x, ai.y));
+        if (lane == 0) {
+          const float4 o = wsm[r];
+          float2 re = make_float2(o.x, o.y), im = make_float2(o.z, o.w);
+          df_add(re, make_float2(t.x, t.y));
+          df_add(im, make_float2(t.z, t.w));
+          re = df_norm(re);
+          im = df_norm(im);
+          wsm[r] = make_float4(re.x, re.y, im.x, im.y);
+        }
       }
+    }
+    __syncthreads();
+    double hv2 = 0.0;
+    for (int r = threadIdx.x; r < nrows; r += kThreads) {
+      const double2 s = cdf_val(wsm[r]);
+      hv2 += s.x * s.x + s.y * s.y;
     }
     hv2 = block_sum(hv2, red1);
     if (threadIdx.x == 0) A.npart[2 * A.grank + 1] = hv2;
@@ -611,8 +700,8 @@ int run_haydock_batch(const HayJob* jobs, int n, int nsteps, const double* omega
     const int e = (int)cudaMemsetAsync(S.bar, 0, 2 * sizeof(unsigned), st);
     if (e) return e;
   }
-  const size_t dyn = ((size_t)B.rows_max + (size_t)nsteps) * sizeof(float4);
-  if (dyn > 160 * 1024) return -1;
+  const size_t dyn = ((size_t)B.rows_max + (size_t)nsteps) * sizeof(float4) + (size_t)kXTile * sizeof(float2);
+  if (dyn > 200 * 1024) return -1;
   cudaFuncSetAttribute((const void*)haydock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, haydock_kernel, kThreads, dyn);
   if (occ < 1) return -1;

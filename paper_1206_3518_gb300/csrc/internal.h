@@ -66,7 +66,9 @@ int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin
                                long long b_count, long long vbase, long long max_rows, const void* W, int prec,
                                void* H, void* ws, int* status, void* stream);
 int launch_gemm_wr_tc(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long vbase,
-                      long long max_rows, const void* W, void* X, int side_c, int* status, void* stream);
+                      long long max_rows, const void* W, void* X, void* split_ws, int side_c, int* status,
+                      void* stream);
+size_t tc_split_bytes(const DevSys& d, long long qchunk);
 size_t kernel_ws_bytes(const DevSys& d, long long qchunk);
 int launch_gemm_wr(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long vbase, long long max_rows,
                    const void* W, void* X, int side_c, void* stream);
