@@ -278,6 +278,19 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
     cp_async_commit();
   };
 
+  // stage-1 items of this thread (fixed for every chunk): line it = tid + k THREADS
+  constexpr int K1 = (PMAX * ROWS + THREADS - 1) / THREADS;
+  int it1[K1], p1[K1], sa1[K1], sb1[K1];
+#pragma unroll
+  for (int k1 = 0; k1 < K1; ++k1) {
+    it1[k1] = tid + k1 * THREADS;
+    p1[k1] = it1[k1] / ROWS;
+    float2* dst_unused;
+    if (it1[k1] < P * ROWS) product_of(d, jb, p1[k1], sa1[k1], sb1[k1], dst_unused);
+  }
+  // stage-3 accumulators: idx = tid + a THREADS -> (p, t) by an incremental walk (no division per slab)
+  const int pa0 = tid / NG, ta0 = tid - (tid / NG) * NG;
+
   issue(0);
   for (int c = 0; c < NCH; ++c) {
     if (c + 1 < NCH) {
@@ -289,11 +302,11 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
     __syncthreads();
     const int j1 = c / CPR, r0 = (c - j1 * CPR) * ROWS;
     const float2* buf = ub + (size_t)(c & 1) * BMAX * ROWS * LD;
-    for (int it = tid; it < P * ROWS; it += THREADS) {          // stage 1: product + z FFT
-      const int p = it / ROWS, row = it - p * ROWS;
-      int sa, sb;
-      float2* dst_unused;
-      product_of(d, jb, p, sa, sb, dst_unused);
+#pragma unroll
+    for (int k1 = 0; k1 < K1; ++k1) {                           // stage 1: product + z FFT
+      if (it1[k1] >= P * ROWS) continue;
+      const int p = p1[k1], row = it1[k1] - p * ROWS;
+      const int sa = sa1[k1], sb = sb1[k1];
       const float4* xa = reinterpret_cast<const float4*>(buf + ((size_t)sa * ROWS + row) * LD);
       const float4* xb = reinterpret_cast<const float4*>(buf + ((size_t)sb * ROWS + row) * LD);
       float2 x[N3];
@@ -321,29 +334,41 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
       }
       for (int g = tid; g < N1; g += THREADS) tw1[g] = fft::tw<N1, true>(c_tw, g * j1);
       __syncthreads();
+      {                                                          // stage 3: x DFT at sphere points
+        int p = pa0, t = ta0;
 #pragma unroll
-      for (int a = 0; a < ACC; ++a) {                            // stage 3: x DFT at sphere points
-        const int idx = tid + a * THREADS;
-        if (idx < P * NG) {
-          const int p = idx / NG, t = idx - p * NG;
-          const int2 g = sg[t];
-          const float2 s = S2[(size_t)p * M2 * M3 + g.y];
-          acc[a] = cadd(acc[a], cmul(s, tw1[g.x]));
+        for (int a = 0; a < ACC; ++a) {
+          if (p < P) {
+            const int2 g = sg[t];
+            const float2 s = S2[(size_t)p * M2 * M3 + g.y];
+            acc[a] = cadd(acc[a], cmul(s, tw1[g.x]));
+          }
+          t += THREADS;
+          while (t >= NG) {
+            t -= NG;
+            ++p;
+          }
         }
       }
     }
     __syncthreads();
   }
   const float inv = 1.0f / (float)(N1 * N2 * N3);
+  {
+    int p = pa0, t = ta0;
 #pragma unroll
-  for (int a = 0; a < ACC; ++a) {
-    const int idx = tid + a * THREADS;
-    if (idx < P * NG) {
-      const int p = idx / NG, t = idx - p * NG;
-      int sa, sb;
-      float2* dst;
-      product_of(d, jb, p, sa, sb, dst);
-      dst[t] = make_float2(acc[a].x * inv, acc[a].y * inv);
+    for (int a = 0; a < ACC; ++a) {
+      if (p < P) {
+        int sa, sb;
+        float2* dst;
+        product_of(d, jb, p, sa, sb, dst);
+        dst[t] = make_float2(acc[a].x * inv, acc[a].y * inv);
+      }
+      t += THREADS;
+      while (t >= NG) {
+        t -= NG;
+        ++p;
+      }
     }
   }
 }
