@@ -330,6 +330,19 @@ def run_stage(args):
     print(json.dumps({"stage": args.only, "config": spec.name, "ms": times, "q_range": [q0, q1], "blocks": nblk}))
 
 
+# DRAM bytes (read + write) of one full-size pair_kernel launch of the fcc 8x8x8 3v4c workload from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass), valid while the kernel
+# sources hash to the recorded value; see profiles/launches_fcc8x8x8_3v4c_fp32.md.
+PAIR_TRAFFIC = {"sha1": "c78b038f9994ae02d2c396a8da137c35cf4ae9ad", "bytes": 94.55e9 + 7.98e9}
+
+
+def _pair_sources_sha1():
+    import hashlib
+    base = os.path.join(ROOT, "paper_1206_3518_gb300", "csrc")
+    data = open(os.path.join(base, "pair.cu"), "rb").read() + open(os.path.join(base, "fft.cuh"), "rb").read()
+    return hashlib.sha1(data).hexdigest()
+
+
 def roofline(stage, ms, spec, inf, peaks, src, nchunks):
     """Algorithmic work of the dominant stage per launch over its measured mean duration."""
     dim = inf["dim"]
@@ -343,7 +356,9 @@ def roofline(stage, ms, spec, inf, peaks, src, nchunks):
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         return {"bound": "alu", "kernel": "pair_kernel", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / peak,
-                "work": "5 N_r log2 N_r FP32 flops per pair-density FFT (FFT convention)", "traffic": None,
+                "work": "5 N_r log2 N_r FP32 flops per pair-density FFT (FFT convention)",
+                "traffic": (PAIR_TRAFFIC["bytes"] if nchunks == 1 and spec.name == "fcc_8x8x8_3v4c"
+                            and _pair_sources_sha1() == PAIR_TRAFFIC["sha1"] else None),
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"}
     if stage == "spectrum":
         bytes_ = spec.nsteps * 8.0 * dim * dim
