@@ -1,19 +1,25 @@
 // Mixed-precision W(q) . rho products on the 5th-generation tensor cores (step A4, BF16x3 form).
 //
-// The complex product X[m][n] = sum_g R[m][g] W[n][g] is a real GEMM
-//   C'[m][2n + c] = sum_k A'[m][k] B'[2n + c][k],   k = 2g + {0, 1},
-// with A' = R read as floats (re, im, re, im, ...), B'[2n] = (Re W, -Im W, ...) and
-// B'[2n+1] = (Im W, Re W, ...), so each accumulator row is the complex64 output row.
-// Every operand is split x = hi + lo in BF16 and C' = A_hi B_hi + A_hi B_lo + A_lo B_hi
-// accumulates in FP32 in tensor memory (relative error ~2^-16 per product).
+// X[m][n] = sum_g R[m][g] W[n][g] (complex) is taken as four real products on separate real and
+// imaginary planes:
+//   Re X = Re R . Re W^T - Im R . Im W^T,   Im X = Re R . Im W^T + Im R . Re W^T,
+// the minus sign coming from the MMA instruction's negate-A bit, so no operand is stored twice.
+// Every operand is split x = hi + lo in BF16 and each real product accumulates
+// hi.hi + hi.lo + lo.hi in FP32 in tensor memory (relative error ~2^-16 per product).
 //
-// One CTA: 128 output rows x 128 complex columns (accumulator 128 lanes x 256 FP32 columns),
-// K in chunks of 64 real values.  All 256 threads convert the next chunk into a 128B-swizzled,
-// K-major shared tile (canonical UMMA layout, 8-row atoms of 1 KB) while the tensor core
-// consumes the previous one; one thread issues tcgen05.mma (M128 N256 K16, 3 splits x 4 steps
-// per chunk) and tcgen05.commit to the chunk's mbarrier.  Every mbarrier wait is bounded by a
-// 2 s %globaltimer limit; on expiry the CTA records BSE_ERR_TIMEOUT, waits once more (bounded)
-// for its own MMAs, frees its tensor memory and returns.
+// Operands are pre-split once per q chunk into the exact shared-memory images the MMA reads:
+// 128-byte rows holding 32 complex K values as [Re(32 BF16) | Im(32 BF16)], 128B-swizzled
+// K-major 8-row atoms.  A tiles are 128 rows of R, B tiles N rows of W (N <= 128, a multiple of
+// 16 chosen so that ceil(NG/N) tiles cover the G range with little padding).
+//
+// tc_gemm_wr is persistent (one CTA per SM, static round-robin over the tiles of the chunk) and
+// warp-specialised: warp 0 streams tile images with bulk copies into a 3-stage ring
+// (transaction-counted mbarriers), warp 1 issues M128 x N x K16 MMAs (12 per 16 complex K), and
+// warps 4-7 drain the accumulator.  Two accumulators (re | im, 256 TMEM columns each) alternate
+// between tiles, so the epilogue of one tile overlaps the MMAs of the next.  Every mbarrier wait
+// is bounded by a 2 s %globaltimer limit; on expiry the CTA records BSE_ERR_TIMEOUT, stops
+// issuing, waits (bounded) for its own copies and MMAs in flight, frees its tensor memory and
+// returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -25,13 +31,15 @@ namespace bse {
 namespace {
 
 constexpr int kTcThreads = 256;
-constexpr int TM = 128;            // output rows per CTA
-constexpr int TN = 256;            // real accumulator columns per CTA (128 complex)
-constexpr int TK = 64;             // real K per chunk (128 bytes of BF16 per row)
-constexpr int kTileA = TM * TK * 2;          // bytes of one A split tile (16 KB)
-constexpr int kTileB = TN * TK * 2;          // bytes of one B split tile (32 KB)
-constexpr int kStage = 2 * kTileA + 2 * kTileB;   // A_hi, A_lo, B_hi, B_lo (96 KB)
-constexpr size_t kTcSmem = 2 * kStage + 1024 + 128;  // two stages, 1 KB alignment slack, barriers
+constexpr int TM = 128;                      // output rows per tile
+constexpr int NMAX = 128;                    // complex output columns per tile, at most
+constexpr int TKC = 32;                      // complex K per stage (one 128-byte row: 32 Re | 32 Im)
+constexpr int kRow = 128;                    // bytes per tile row
+constexpr int kTileA = TM * kRow;            // one split of an A tile (16 KB)
+constexpr int kStages = 3;
+constexpr int kStage = 2 * kTileA + 2 * NMAX * kRow;   // A hi, A lo, B hi, B lo (64 KB at N = 128)
+constexpr int kAccCols = 256;                // one accumulator: Re in columns [0,128), Im in [128,256)
+constexpr size_t kTcSmem = (size_t)kStages * kStage + 1024 + 256;   // ring, 1 KB alignment slack, barriers
 
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
@@ -60,6 +68,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // UMMA shared-memory descriptor: K-major, 128B swizzle, 8-row atoms 1024 B apart.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
@@ -71,14 +83,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor: D f32, A/B bf16, both K-major, M = 128, N = 256.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// Instruction descriptor: D f32, A/B bf16, both K-major, M = 128, N = n; bit 13 negates A.
+__host__ __device__ constexpr uint32_t idesc_of(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+constexpr uint32_t kNegA = 1u << 13;
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(da), "l"(db), "r"(kIdesc), "r"(acc)
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
       : "memory");
 }
 
@@ -87,7 +102,7 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 }
 
 // 16-byte chunk c of row r of a swizzled K-major tile (rows of 128 bytes).
-__device__ __forceinline__ uint32_t swz(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+__device__ __forceinline__ uint32_t swz(int r, int c) { return (uint32_t)(r * kRow + ((c ^ (r & 7)) << 4)); }
 
 __device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
   __nv_bfloat162 h[4], l[4];
@@ -103,10 +118,8 @@ __device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo
 }
 
 // ---------------------------------------------------------------- operand split (one pass per q chunk)
-// Tile images are exactly the shared-memory images the MMA reads: A tiles 128 rows x 64 BF16 (hi 16 KB
-// then lo 16 KB), B tiles 256 rows x 64 BF16 (hi 32 KB then lo 32 KB), addressed by (q, row tile, k chunk).
 struct SplitGeo {
-  int q_begin, mt_max, nt_max, kc_max;
+  int q_begin, nq, mt_max, nt_max, kc_max, n_tile;
   long long vbase;
   int side_c;
 };
@@ -115,7 +128,24 @@ __device__ __forceinline__ size_t a_tile_off(const SplitGeo& g, int qi, int mt, 
   return (((size_t)qi * g.mt_max + mt) * g.kc_max + c) * (size_t)(2 * kTileA);
 }
 __device__ __forceinline__ size_t b_tile_off(const SplitGeo& g, int qi, int nt, int c) {
-  return (((size_t)qi * g.nt_max + nt) * g.kc_max + c) * (size_t)(2 * kTileB);
+  return (((size_t)qi * g.nt_max + nt) * g.kc_max + c) * (size_t)(2 * g.n_tile * kRow);
+}
+
+// Row r of a tile image from 8 complex values v: chunk cq holds Re, chunk 4 + cq holds Im.
+__device__ __forceinline__ void put_row8(unsigned char* hi, unsigned char* lo, int r, int cq, const float2 (&v)[8]) {
+  float xr[8], xi[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    xr[i] = v[i].x;
+    xi[i] = v[i].y;
+  }
+  uint4 hr, lr, hi2, li2;
+  split8(xr, hr, lr);
+  split8(xi, hi2, li2);
+  *reinterpret_cast<uint4*>(hi + swz(r, cq)) = hr;
+  *reinterpret_cast<uint4*>(lo + swz(r, cq)) = lr;
+  *reinterpret_cast<uint4*>(hi + swz(r, 4 + cq)) = hi2;
+  *reinterpret_cast<uint4*>(lo + swz(r, 4 + cq)) = li2;
 }
 
 __global__ __launch_bounds__(kTcThreads) void split_a_kernel(DevSys d, const float2* __restrict__ rho_dir,
@@ -124,22 +154,20 @@ __global__ __launch_bounds__(kTcThreads) void split_a_kernel(DevSys d, const flo
   const int q = g.q_begin + qi;
   const long long nblk = d.qblk_off[q + 1] - d.qblk_off[q];
   const int w = g.side_c ? d.nc * d.nc : d.nv * d.nv;
-  const int M = (int)(nblk * w), NG = d.ngq[q], Kr = 2 * NG;
-  if (mt * TM >= M || c * TK >= Kr) return;
+  const int M = (int)(nblk * w), NG = d.ngq[q];
+  if (mt * TM >= M || c * TKC >= NG) return;
   long long aoff = d.qvec_off[q] - g.vbase;
   if (g.side_c) aoff += nblk * d.nv * d.nv;
-  const float* A = reinterpret_cast<const float*>(rho_dir + (size_t)aoff * d.ng_max);
-  unsigned char* dst = As + a_tile_off(g, qi, mt, c);
-  for (int it = threadIdx.x; it < TM * 8; it += kTcThreads) {
-    const int r = it >> 3, ch = it & 7;
-    const int row = mt * TM + r, kk = c * TK + 8 * ch;
-    float x[8];
+  const float2* A = rho_dir + (size_t)aoff * d.ng_max;
+  unsigned char* hi = As + a_tile_off(g, qi, mt, c);
+  for (int it = threadIdx.x; it < TM * 4; it += kTcThreads) {
+    const int r = it >> 2, cq = it & 3;
+    const int row = mt * TM + r, g0 = c * TKC + 8 * cq;
+    float2 v[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) x[i] = (row < M && kk + i < Kr) ? A[(size_t)row * (2 * d.ng_max) + kk + i] : 0.f;
-    uint4 hi, lo;
-    split8(x, hi, lo);
-    *reinterpret_cast<uint4*>(dst + swz(r, ch)) = hi;
-    *reinterpret_cast<uint4*>(dst + kTileA + swz(r, ch)) = lo;
+    for (int i = 0; i < 8; ++i)
+      v[i] = (row < M && g0 + i < NG) ? A[(size_t)row * d.ng_max + g0 + i] : make_float2(0.f, 0.f);
+    put_row8(hi, hi + kTileA, r, cq, v);
   }
 }
 
@@ -147,32 +175,18 @@ __global__ __launch_bounds__(kTcThreads) void split_b_kernel(DevSys d, const flo
                                                              unsigned char* __restrict__ Bs, SplitGeo g) {
   const int c = blockIdx.x, nt = blockIdx.y, qi = blockIdx.z;
   const int q = g.q_begin + qi;
-  const int NG = d.ngq[q];
-  if (nt * (TN / 2) >= NG || c * TK >= 2 * NG) return;
+  const int NG = d.ngq[q], N = g.n_tile;
+  if (nt * N >= NG || c * TKC >= NG) return;
   const float2* Wq = W + (size_t)q * d.ng_max * d.ng_max;
-  unsigned char* bh = Bs + b_tile_off(g, qi, nt, c);
-  unsigned char* bl = bh + kTileB;
-  for (int it = threadIdx.x; it < (TN / 2) * 8; it += kTcThreads) {
-    const int n = it >> 3, ch = it & 7;
-    const int col = nt * (TN / 2) + n;
-    const int g0 = (c * TK >> 1) + 4 * ch;
-    float xr[8], xi[8];
+  unsigned char* hi = Bs + b_tile_off(g, qi, nt, c);
+  for (int it = threadIdx.x; it < N * 4; it += kTcThreads) {
+    const int n = it >> 2, cq = it & 3;
+    const int col = nt * N + n, g0 = c * TKC + 8 * cq;
+    float2 v[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float2 v = make_float2(0.f, 0.f);
-      if (col < NG && g0 + i < NG) v = Wq[(size_t)col * d.ng_max + g0 + i];
-      xr[2 * i] = v.x;
-      xr[2 * i + 1] = -v.y;
-      xi[2 * i] = v.y;
-      xi[2 * i + 1] = v.x;
-    }
-    uint4 hr, lr, hi2, li2;
-    split8(xr, hr, lr);
-    split8(xi, hi2, li2);
-    *reinterpret_cast<uint4*>(bh + swz(2 * n, ch)) = hr;
-    *reinterpret_cast<uint4*>(bl + swz(2 * n, ch)) = lr;
-    *reinterpret_cast<uint4*>(bh + swz(2 * n + 1, ch)) = hi2;
-    *reinterpret_cast<uint4*>(bl + swz(2 * n + 1, ch)) = li2;
+    for (int i = 0; i < 8; ++i)
+      v[i] = (col < NG && g0 + i < NG) ? Wq[(size_t)col * d.ng_max + g0 + i] : make_float2(0.f, 0.f);
+    put_row8(hi, hi + N * kRow, n, cq, v);
   }
 }
 
@@ -193,38 +207,67 @@ struct TcArgs {
   int* status;
 };
 
-// Warp-specialised GEMM on the split tiles: warp 0 streams tiles (bulk copies, transaction-counted
-// mbarriers), warp 1 issues the MMAs, warps 4..7 drain the accumulator.  Two stages of 96 KB.
+// Tile t of the chunk (N tiles fastest, then row tiles, then q); false if it holds no output.
+struct Tile {
+  int qi, q, mt, nt, M, NG, nch;
+};
+__device__ __forceinline__ bool tile_of(const DevSys& d, const SplitGeo& g, int w, long long t, Tile& o) {
+  o.nt = (int)(t % g.nt_max);
+  const long long r = t / g.nt_max;
+  o.mt = (int)(r % g.mt_max);
+  o.qi = (int)(r / g.mt_max);
+  o.q = g.q_begin + o.qi;
+  const long long nblk = d.qblk_off[o.q + 1] - d.qblk_off[o.q];
+  o.M = (int)(nblk * w);
+  o.NG = d.ngq[o.q];
+  o.nch = (o.NG + TKC - 1) / TKC;
+  return o.mt * TM < o.M && o.nt * g.n_tile < o.NG;
+}
+
+__device__ __forceinline__ void fail_now(volatile int* fail, int* status) {
+  *fail = 1;
+  atomicCAS(status, 0, (int)BSE_ERR_TIMEOUT);
+}
+
 __global__ __launch_bounds__(kTcThreads, 1) void tc_gemm_wr(DevSys d, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(sm + 2 * kStage);        // [2] tiles landed
-  uint64_t* empty = full + 2;                           // [2] MMAs done with the stage
-  uint64_t* accum = full + 4;                           // accumulator complete
-  uint32_t* tmem_slot = (uint32_t*)(sm + 2 * kStage + 48);
-  volatile int* fail = (volatile int*)(sm + 2 * kStage + 56);
+  uint64_t* full = (uint64_t*)(sm + kStages * kStage);   // [3] stage landed
+  uint64_t* empty = full + kStages;                       // [3] MMAs done with the stage
+  uint64_t* tfull = empty + kStages;                      // [2] accumulator complete
+  uint64_t* tempty = tfull + 2;                           // [2] accumulator drained
+  uint64_t* drain = tempty + 2;                           // all MMAs of this CTA complete
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* fail = (volatile int*)(tmem_slot + 1);
+  volatile unsigned* issued = (volatile unsigned*)(tmem_slot + 2);
+  volatile unsigned* consumed = (volatile unsigned*)(tmem_slot + 3);
 
   const SplitGeo& g = a.g;
-  const int qi = blockIdx.z, q = g.q_begin + qi;
-  const long long b0 = d.qblk_off[g.q_begin];
-  const long long nblk = d.qblk_off[q + 1] - d.qblk_off[q];
+  const int N = g.n_tile;
   const int w = g.side_c ? d.nc * d.nc : d.nv * d.nv;
-  const int M = (int)(nblk * w), NG = d.ngq[q];
-  const int mt = blockIdx.y, nt = blockIdx.x;
-  const int m0 = mt * TM, n0 = nt * (TN / 2);
-  if (m0 >= M || n0 >= NG) return;
-  const int nch = (2 * NG + TK - 1) / TK;
+  const long long b0 = d.qblk_off[g.q_begin];
+  const long long ntiles = (long long)g.nq * g.mt_max * g.nt_max;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TN)
+                 "r"(2 * kAccCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 32) {
-    for (int i = 0; i < 5; ++i) mbar_init(smem_u32(full + i), 1);
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(smem_u32(full + i), 1);
+      mbar_init(smem_u32(empty + i), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(tfull + i), 1);
+      mbar_init(smem_u32(tempty + i), 4);
+    }
+    mbar_init(smem_u32(drain), 1);
     *fail = 0;
+    *issued = 0;
+    *consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -233,56 +276,97 @@ __global__ __launch_bounds__(kTcThreads, 1) void tc_gemm_wr(DevSys d, TcArgs a) 
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {                 // producer
-    for (int c = 0; c < nch; ++c) {
-      const int st = c & 1;
-      if (c >= 2 && !mbar_wait(smem_u32(empty + st), (uint32_t)(((c - 2) >> 1) & 1))) {
-        *fail = 1;
-        break;
+    const uint32_t bbytes = (uint32_t)(2 * N * kRow);
+    unsigned c = 0;
+    Tile t;
+    for (long long ti = blockIdx.x; ti < ntiles && !*fail; ti += gridDim.x) {
+      if (!tile_of(d, g, w, ti, t)) continue;
+      for (int kc = 0; kc < t.nch; ++kc, ++c) {
+        const int st = (int)(c % kStages);
+        if (c >= kStages && !mbar_wait(smem_u32(empty + st), ((c / kStages) - 1) & 1u)) {
+          fail_now(fail, a.status);
+          break;
+        }
+        if (*fail) break;
+        const uint32_t base = smem_u32(sm + st * kStage);
+        mbar_expect_tx(smem_u32(full + st), (uint32_t)(2 * kTileA) + bbytes);
+        bulk_g2s(base, a.As + a_tile_off(g, t.qi, t.mt, kc), 2 * kTileA, smem_u32(full + st));
+        bulk_g2s(base + 2 * kTileA, a.Bs + b_tile_off(g, t.qi, t.nt, kc), bbytes, smem_u32(full + st));
+        *issued = c + 1;
       }
-      if (*fail) break;
-      const uint32_t base = smem_u32(sm + st * kStage);
-      mbar_expect_tx(smem_u32(full + st), (uint32_t)kStage);
-      bulk_g2s(base, a.As + a_tile_off(g, qi, mt, c), 2 * kTileA, smem_u32(full + st));
-      bulk_g2s(base + 2 * kTileA, a.Bs + b_tile_off(g, qi, nt, c), 2 * kTileB, smem_u32(full + st));
     }
   } else if (warp == 1 && lane == 0) {          // MMA issuer
+    const uint32_t idesc = idesc_of(N), idesc_neg = idesc | kNegA;
+    unsigned c = 0, j = 0;
+    Tile t;
     bool ok = true;
-    for (int c = 0; c < nch; ++c) {
-      const int st = c & 1;
-      if (!mbar_wait(smem_u32(full + st), (uint32_t)((c >> 1) & 1))) {
-        *fail = 1;
+    for (long long ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+      if (!tile_of(d, g, w, ti, t)) continue;
+      const int buf = (int)(j & 1);
+      if (j >= 2 && !mbar_wait(smem_u32(tempty + buf), ((j >> 1) - 1) & 1u)) {
+        fail_now(fail, a.status);
         ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = smem_u32(sm + st * kStage);
-      const uint32_t sah = sa, sal = sa + kTileA, sbh = sa + 2 * kTileA, sbl = sbh + kTileB;
+      const uint32_t d_re = tmem + (uint32_t)(buf * kAccCols), d_im = d_re + 128;
+      for (int kc = 0; kc < t.nch; ++kc, ++c) {
+        const int st = (int)(c % kStages);
+        if (!mbar_wait(smem_u32(full + st), (c / kStages) & 1u) || *fail) {
+          fail_now(fail, a.status);
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sah = smem_u32(sm + st * kStage), sal = sah + kTileA;
+        const uint32_t sbh = sah + 2 * kTileA, sbl = sbh + (uint32_t)(N * kRow);
+        const int nkk = (t.NG - kc * TKC > 16) ? 2 : 1;   // the last chunk may need one K16 step only
 #pragma unroll
-      for (int s = 0; s < 3; ++s) {
-        const uint32_t pa = (s == 2) ? sal : sah;
-        const uint32_t pb = (s == 1) ? sbl : sbh;
+        for (int kk = 0; kk < 2; ++kk) {
+          if (kk >= nkk) break;
 #pragma unroll
-        for (int kk = 0; kk < TK / 16; ++kk)
-          mma_bf16(tmem, smem_desc(pa + kk * 32), smem_desc(pb + kk * 32), (c | s | kk) != 0 ? 1u : 0u);
+          for (int s = 0; s < 3; ++s) {           // hi.hi, hi.lo, lo.hi
+            const uint32_t pa = ((s == 2) ? sal : sah) + kk * 32, pb = ((s == 1) ? sbl : sbh) + kk * 32;
+            const uint32_t acc = (kc | kk | s) != 0 ? 1u : 0u;
+            mma_bf16(d_re, smem_desc(pa), smem_desc(pb), idesc, acc);                // Re R Re W
+            mma_bf16(d_re, smem_desc(pa + 64), smem_desc(pb + 64), idesc_neg, 1u);   // - Im R Im W
+            mma_bf16(d_im, smem_desc(pa), smem_desc(pb + 64), idesc, acc);           // Re R Im W
+            mma_bf16(d_im, smem_desc(pa + 64), smem_desc(pb), idesc, 1u);            // Im R Re W
+          }
+        }
+        mma_commit(smem_u32(empty + st));
+        *consumed = c + 1;
       }
-      mma_commit(smem_u32(empty + st));
+      if (!ok) break;
+      mma_commit(smem_u32(tfull + buf));
+      ++j;
     }
-    if (ok) mma_commit(smem_u32(accum));
+    mma_commit(smem_u32(drain));                // tracks every MMA issued above
+    if (!mbar_wait(smem_u32(drain), 0u)) fail_now(fail, a.status);
   } else if (warp >= 4) {                       // epilogue: TMEM lanes 32(w-4).. -> output rows
     const int ew = warp - 4;
-    bool ok = mbar_wait(smem_u32(accum), 0u);
-    if (!ok) {
-      if (lane == 0) atomicCAS(a.status, 0, (int)BSE_ERR_TIMEOUT);
-      *fail = 1;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
+    const bool even = (d.ng_max & 1) == 0;
+    unsigned j = 0;
+    Tile t;
+    for (long long ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+      if (!tile_of(d, g, w, ti, t)) continue;
+      const int buf = (int)(j & 1);
+      int ok = 1;
+      if (lane == 0) {
+        ok = mbar_wait(smem_u32(tfull + buf), (j >> 1) & 1u) ? 1 : 0;
+        if (!ok) fail_now(fail, a.status);
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int m0 = t.mt * TM, n0 = t.nt * N;
       const int r = m0 + ew * 32 + lane;
-      float2* out = a.X + (size_t)((d.qblk_off[q] - b0) * w + r) * d.ng_max;
+      float2* out = a.X + (size_t)((d.qblk_off[t.q] - b0) * w + r) * d.ng_max;
+      const int nvalid = min(N, t.NG - n0);
 #pragma unroll 1
-      for (int c0 = 0; c0 < TN; c0 += 32) {
-        uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)c0;
+      for (int c0 = 0; c0 < N; c0 += 32) {
+        uint32_t v[32], u[32];
+        const uint32_t taddr = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(buf * kAccCols + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -293,59 +377,111 @@ __global__ __launch_bounds__(kTcThreads, 1) void tc_gemm_wr(DevSys d, TcArgs a) 
               "=r"(v[30]), "=r"(v[31])
             : "r"(taddr)
             : "memory");
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+              "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
+              "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]),
+              "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]),
+              "=r"(u[30]), "=r"(u[31])
+            : "r"(taddr + 128u)
+            : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (r < M) {
+        const int cnt = min(32, nvalid - c0);
+        if (r < t.M && cnt > 0) {
+          float2* o = out + n0 + c0;
+          if (even) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int n = n0 + c0 / 2 + i;
-            if (n < NG) out[n] = make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+            for (int i = 0; i < 16; ++i) {
+              if (2 * i + 1 < cnt)
+                *reinterpret_cast<float4*>(o + 2 * i) = make_float4(__uint_as_float(v[2 * i]), __uint_as_float(u[2 * i]),
+                                                                    __uint_as_float(v[2 * i + 1]),
+                                                                    __uint_as_float(u[2 * i + 1]));
+              else if (2 * i < cnt)
+                o[2 * i] = make_float2(__uint_as_float(v[2 * i]), __uint_as_float(u[2 * i]));
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (i < cnt) o[i] = make_float2(__uint_as_float(v[i]), __uint_as_float(u[i]));
           }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(tempty + buf));
+      ++j;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
+  if (tid == 0) {                               // copies still in flight after a failure
+    for (unsigned c = *consumed; c < *issued; ++c)
+      if (!mbar_wait(smem_u32(full + c % kStages), (c / kStages) & 1u)) break;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kAccCols) : "memory");
+  }
+}
+
+// N tile: ceil(ng_max / ceil(ng_max / 128)) rounded up to 16.
+int tc_n_tile(const DevSys& d) {
+  const int nt = (d.ng_max + NMAX - 1) / NMAX;
+  const int n = (d.ng_max + nt - 1) / nt;
+  return (n + 15) / 16 * 16;
 }
 
 }  // namespace
 
 size_t tc_split_bytes(const DevSys& d, long long qchunk) {
   const long long w = (d.nv * d.nv <= d.nc * d.nc) ? d.nv * d.nv : d.nc * d.nc;
-  const long long mt = (d.nkpt * w + TM - 1) / TM, nt = (d.ng_max + TN / 2 - 1) / (TN / 2);
-  const long long kc = (2 * d.ng_max + TK - 1) / TK;
-  return (size_t)qchunk * (size_t)kc * ((size_t)mt * 2 * kTileA + (size_t)nt * 2 * kTileB);
+  const int N = tc_n_tile(d);
+  const long long mt = (d.nkpt * w + TM - 1) / TM, nt = (d.ng_max + N - 1) / N;
+  const long long kc = (d.ng_max + TKC - 1) / TKC;
+  return (size_t)qchunk * (size_t)kc * ((size_t)mt * 2 * kTileA + (size_t)nt * 2 * N * kRow);
 }
 
 // ws holds the split tiles; X is the FP32 output of the products.
 int launch_gemm_wr_tc(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long vbase,
                       long long max_rows, const void* W, void* X, void* split_ws, int side_c, int* status,
                       void* stream) {
-  static bool attr = false;
-  if (!attr) {
-    const int e = (int)cudaFuncSetAttribute((const void*)tc_gemm_wr, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)kTcSmem);
+  static int attr_dev = -1, num_sms = 0;
+  int dev = 0;
+  int e = (int)cudaGetDevice(&dev);
+  if (e) return e;
+  if (attr_dev != dev) {
+    e = (int)cudaFuncSetAttribute((const void*)tc_gemm_wr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kTcSmem);
     if (e) return e;
-    attr = true;
+    e = (int)cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e) return e;
+    attr_dev = dev;
   }
   cudaStream_t st = (cudaStream_t)stream;
   SplitGeo g;
   g.q_begin = q_begin;
+  g.nq = q_end - q_begin;
   g.vbase = vbase;
   g.side_c = side_c;
+  g.n_tile = tc_n_tile(d);
   g.mt_max = (int)((max_rows + TM - 1) / TM);
-  g.nt_max = (d.ng_max + TN / 2 - 1) / (TN / 2);
-  g.kc_max = (2 * d.ng_max + TK - 1) / TK;
-  const int nq = q_end - q_begin;
+  g.nt_max = (d.ng_max + g.n_tile - 1) / g.n_tile;
+  g.kc_max = (d.ng_max + TKC - 1) / TKC;
   unsigned char* As = (unsigned char*)split_ws;
-  unsigned char* Bs = As + (size_t)nq * g.mt_max * g.kc_max * 2 * kTileA;
-  split_a_kernel<<<dim3(g.kc_max, g.mt_max, nq), kTcThreads, 0, st>>>(d, (const float2*)rho_dir, As, g);
-  split_b_kernel<<<dim3(g.kc_max, g.nt_max, nq), kTcThreads, 0, st>>>(d, (const float2*)W, Bs, g);
-  int e = (int)cudaGetLastError();
+  unsigned char* Bs = As + (size_t)g.nq * g.mt_max * g.kc_max * 2 * kTileA;
+  split_a_kernel<<<dim3(g.kc_max, g.mt_max, g.nq), kTcThreads, 0, st>>>(d, (const float2*)rho_dir, As, g);
+  split_b_kernel<<<dim3(g.kc_max, g.nt_max, g.nq), kTcThreads, 0, st>>>(d, (const float2*)W, Bs, g);
+  e = (int)cudaGetLastError();
   if (e) return e;
   TcArgs a{As, Bs, (float2*)X, g, status};
-  tc_gemm_wr<<<dim3(g.nt_max, g.mt_max, nq), kTcThreads, kTcSmem, st>>>(d, a);
+  const long long ntiles = (long long)g.nq * g.mt_max * g.nt_max;
+  const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
+  if (grid <= 0) return 0;
+  tc_gemm_wr<<<grid, kTcThreads, kTcSmem, st>>>(d, a);
   return (int)cudaGetLastError();
 }
 
