@@ -55,9 +55,9 @@ bse_status cuda_check(int err, const char* what);
 
 // Kernel launchers (defined in the .cu files); all return cudaError_t as int.
 int launch_realspace(const DevSys& d, const void* coef, void* u, void* stream);
-int launch_pair_exchange(const DevSys& d, const void* u, void* rho_x, void* stream);
+int launch_pair_exchange(const DevSys& d, const void* u, void* rho_x, int* status, void* stream);
 int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, int q_begin, int q_end, long long vbase,
-                       void* stream);
+                       int* status, void* stream);
 int launch_dipole(const DevSys& d, const void* coef, const double* energies, double gap_floor, void* P, void* stream);
 int pair_supported(const DevSys& d);
 

@@ -10,15 +10,21 @@
 //
 // A2 (pair_kernel): one CTA per job = (k, k', band set n, band set m).  The grid is
 // streamed in x-slabs, ROWS z-lines at a time, for every band of the job (each
-// u_nk line read once per job and reused by all |m| products).  Per slab:
+// u_nk line read once per job and reused by all |m| products): one 2D tensor copy
+// (TMA) per band and chunk into a double buffer, completion counted on an mbarrier
+// per buffer.  The copy box is N3 + 2 wide so that the two out-of-bounds columns
+// (filled with zeros) pad the shared rows for conflict-free float4 reads.  Per slab:
 //   stage 1: each thread forms conj(u_n) u_m along one z-line and FFTs it in
 //            registers, keeping |f3| <= F3;
 //   stage 2: y-line FFTs of the kept planes, keeping |f2| <= F2;
 //   stage 3: the x direction is a direct DFT accumulated over slabs, evaluated
-//            only at the sphere points (register accumulators).
+//            only at the sphere points (register accumulators; each thread owns
+//            sphere points and accumulates every product there).
 // Work therefore scales with the kept windows rather than with N^3 log N in the
 // last two passes.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 
@@ -69,7 +75,7 @@ __global__ __launch_bounds__(kThreads) void realspace_kernel(DevSys d, const flo
     for (int j = 0; j < N1; ++j) x[j] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int f = -F1; f <= F1; ++f) x[(f + N1) % N1] = box[(f + F1) * M2 * M3 + it];
-    fft::line<N1, false>(c_tw, x);
+    fft::line<N1, false>(x);
 #pragma unroll
     for (int j = 0; j < N1; ++j) T1[j * M2 * M3 + it] = x[j];
   }
@@ -83,7 +89,7 @@ __global__ __launch_bounds__(kThreads) void realspace_kernel(DevSys d, const flo
       for (int j = 0; j < N2; ++j) y[j] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int f = -F2; f <= F2; ++f) y[(f + N2) % N2] = T1[((s0 + jj) * M2 + (f + F2)) * M3 + m3];
-      fft::line<N2, false>(c_tw, y);
+      fft::line<N2, false>(y);
 #pragma unroll
       for (int j = 0; j < N2; ++j) T2[(jj * N2 + j) * M3 + m3] = y[j];
     }
@@ -95,7 +101,7 @@ __global__ __launch_bounds__(kThreads) void realspace_kernel(DevSys d, const flo
       for (int j = 0; j < N3; ++j) z[j] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int f = -F3; f <= F3; ++f) z[(f + N3) % N3] = T2[(jj * N2 + j2) * M3 + (f + F3)];
-      fft::line<N3, false>(c_tw, z);
+      fft::line<N3, false>(z);
       float4* dst = reinterpret_cast<float4*>(dst0 + ((size_t)(s0 + jj) * N2 + j2) * N3);
 #pragma unroll
       for (int j = 0; j < N3 / 2; ++j) dst[j] = make_float4(z[2 * j].x, z[2 * j].y, z[2 * j + 1].x, z[2 * j + 1].y);
@@ -106,18 +112,21 @@ __global__ __launch_bounds__(kThreads) void realspace_kernel(DevSys d, const flo
 
 // ---------------------------------------------------------------- A2
 // Template parameters: grid N1 x N2 x N3; kept windows |f2| <= F2, |f3| <= F3; PMAX band
-// products and BMAX band slabs per CTA; ROWS z-lines per pipelined chunk; ACC sphere
-// accumulators per thread; THREADS per CTA; MERGED = one CTA computes both the vv' and
-// the cc' products of a block (else one CTA per block and group).
-template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int ACC, int THREADS, bool MERGED>
+// products and BMAX band slabs per CTA; ROWS z-lines per pipelined chunk; PPT sphere points
+// per thread in stage 3; THREADS per CTA; MERGED = one CTA computes both the vv' and the cc'
+// products of a block (else one CTA per block and group).
+template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int PPT, int THREADS, bool MERGED>
 struct PairCfg {
   static constexpr int M2 = 2 * F2 + 1, M3 = 2 * F3 + 1;
   static constexpr int LD = N3 + 2;    // z-line stride in shared memory: 16-B aligned rows, float4 reads conflict-free
   static constexpr int NCH = N1 * (N2 / ROWS);
   static_assert(N2 % ROWS == 0, "ROWS must divide N2");
+  static_assert(BMAX <= THREADS, "one band copy per thread and chunk");
+  static_assert(((N3 + 2) * 8) % 16 == 0, "copy box rows are 16-byte multiples");
   static constexpr int S1P = (N2 + 1) * M3;   // product stride of S1 (one padding row: spreads banks)
+  static constexpr int BSTR = (ROWS * LD * 8 + 127) / 128 * 16;   // band stride in float2: 128-byte multiple
   static size_t smem(int ng_max) {
-    return sizeof(float2) * ((size_t)2 * BMAX * ROWS * LD + (size_t)PMAX * S1P + (size_t)PMAX * M2 * M3 + N1) +
+    return 24 + sizeof(float2) * ((size_t)2 * BMAX * BSTR + (size_t)PMAX * S1P + (size_t)PMAX * M2 * M3 + N1) +
            sizeof(int2) * (size_t)ng_max;
   }
 };
@@ -219,31 +228,68 @@ __device__ __forceinline__ void product_of(const DevSys& d, const Job& j, int p,
   }
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int ACC, int THREADS, bool MERGED>
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait on an mbarrier phase; false after 2 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (gtimer() - t0 > 2000000000ull) return false;
+  }
+}
+
+template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int PPT, int THREADS, bool MERGED>
 __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2* __restrict__ u,
                                                           float2* __restrict__ out, int mode, int q0, int nqc,
-                                                          long long vbase) {
-  using C = PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, ACC, THREADS, MERGED>;
-  constexpr int M2 = C::M2, M3 = C::M3, LD = C::LD, NCH = C::NCH, S1P = C::S1P;
+                                                          long long vbase, int* status,
+                                                          const __grid_constant__ CUtensorMap tm) {
+  using C = PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, PPT, THREADS, MERGED>;
+  constexpr int M2 = C::M2, M3 = C::M3, LD = C::LD, NCH = C::NCH, S1P = C::S1P, BSTR = C::BSTR;
   constexpr int CPR = N2 / ROWS;            // chunks per slab
-  extern __shared__ float4 sm4[];
-  float2* ub = reinterpret_cast<float2*>(sm4);   // [2][BMAX][ROWS][LD]
-  float2* S1 = ub + 2 * BMAX * ROWS * LD;         // [PMAX][N2 (+1 pad)][M3]
-  float2* S2 = S1 + PMAX * S1P;                   // [PMAX][M2][M3]
-  float2* tw1 = S2 + PMAX * M2 * M3;              // [N1] exp(-2 pi i g j1/N1) of the current slab
-  int2* sg = reinterpret_cast<int2*>(tw1 + N1);
+  extern __shared__ __align__(128) float4 sm4[];
+  float2* ub = reinterpret_cast<float2*>(sm4);          // [2][BMAX][BSTR]: ROWS rows of LD per band
+  float2* S1 = ub + 2 * BMAX * BSTR;                    // [PMAX][N2 (+1 pad)][M3]
+  float2* S2 = S1 + PMAX * S1P;                         // [PMAX][M2][M3]
+  float2* tw1 = S2 + PMAX * M2 * M3;                    // [N1] exp(-2 pi i g j1/N1) of the current slab
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tw1 + N1);   // [2] chunk landed (one per buffer)
+  volatile int& s_fail = *reinterpret_cast<volatile int*>(bars + 2);
+  int2* sg = reinterpret_cast<int2*>(bars + 3);
 
   Job jb;
   if (!decode_job(d, mode, MERGED, q0, nqc, vbase, out, jb)) return;
   const int tid = threadIdx.x;
+  if (smem_u32(sm4) & 127u) {               // box copies need 128-byte aligned destinations
+    if (tid == 0) atomicCAS(status, 0, (int)BSE_ERR_CUDA);
+    return;
+  }
+  const uint32_t bar0 = smem_u32(bars);
+  if (tid == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar0 + 8, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   const int P = (jb.mode == 0) ? d.nv * d.nc
               : (jb.mode == 1) ? d.nv * d.nv
               : (jb.mode == 2) ? d.nc * d.nc : d.nv * d.nv + d.nc * d.nc;
@@ -253,31 +299,34 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
     const int G1 = g.x - jb.g0x, G2 = g.y - jb.g0y, G3 = g.z - jb.g0z;   // G = g_p - G0
     sg[t] = make_int2(((G1 % N1) + N1) % N1, (G2 + F2) * M3 + (G3 + F3));
   }
-  float2 acc[ACC];
+  float2 acc[PPT * PMAX];
 #pragma unroll
-  for (int a = 0; a < ACC; ++a) acc[a] = make_float2(0.f, 0.f);
+  for (int a = 0; a < PPT * PMAX; ++a) acc[a] = make_float2(0.f, 0.f);
 
-  const size_t vol = (size_t)N1 * N2 * N3;
-  const float2* ua = u + ((size_t)jb.k * d.nb + jb.a0) * vol;
-  const float2* ubb = u + ((size_t)jb.k2 * d.nb + jb.b0) * vol;
+  // loads: thread tid < nbands copies band tid's ROWS z-lines of each chunk as one 2D box (LD x ROWS;
+  // the two columns past N3 are out of bounds and arrive as zeros)
   const int nbands = jb.na + jb.nb;
+  long long lbase = 0;
+  if (tid < nbands)
+    lbase = (tid < jb.na) ? ((long long)jb.k * d.nb + jb.a0 + tid) * (N1 * N2)
+                          : ((long long)jb.k2 * d.nb + jb.b0 + tid - jb.na) * (N1 * N2);
+  constexpr uint32_t kBox = ROWS * LD * sizeof(float2), kBand = BSTR * sizeof(float2), kBuf = BMAX * kBand;
+  const uint32_t chunk_bytes = (uint32_t)nbands * kBox;
+  const uint32_t ldst = smem_u32(ub) + (uint32_t)tid * kBand;
+  __syncthreads();                          // barriers initialised, sphere table filled
 
   auto issue = [&](int c) {
     const int j1 = c / CPR, r0 = (c - j1 * CPR) * ROWS;
-    float2* dstb = ub + (size_t)(c & 1) * BMAX * ROWS * LD;
-    constexpr int H = N3 / 2;               // 16-byte pieces per z-line; a chunk is ROWS contiguous lines
-    const size_t goff = ((size_t)j1 * N2 + r0) * N3;
-    for (int bi = 0; bi < nbands; ++bi) {
-      const float2* src = ((bi < jb.na) ? ua + (size_t)bi * vol : ubb + (size_t)(bi - jb.na) * vol) + goff;
-      float2* dst = dstb + (size_t)bi * ROWS * LD;
-      for (int e = tid; e < ROWS * H; e += THREADS) {
-        const int row = e / H, h = e - row * H;
-        cp_async16(dst + row * LD + 2 * h, src + 2 * e);
-      }
+    const uint32_t bar = bar0 + 8u * (uint32_t)(c & 1);
+    if (tid == 0) mbar_expect_tx(bar, chunk_bytes);
+    if (tid < nbands) {
+      const int y = (int)(lbase + j1 * N2 + r0);
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+          ::"r"(ldst + (uint32_t)(c & 1) * kBuf), "l"(reinterpret_cast<uint64_t>(&tm)), "r"(0), "r"(y), "r"(bar)
+          : "memory");
     }
-    cp_async_commit();
   };
-
   // stage-1 items of this thread (fixed for every chunk): line it = tid + k THREADS
   constexpr int K1 = (PMAX * ROWS + THREADS - 1) / THREADS;
   int it1[K1], p1[K1], sa1[K1], sb1[K1];
@@ -288,27 +337,30 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
     float2* dst_unused;
     if (it1[k1] < P * ROWS) product_of(d, jb, p1[k1], sa1[k1], sb1[k1], dst_unused);
   }
-  // stage-3 accumulators: idx = tid + a THREADS -> (p, t) by an incremental walk (no division per slab)
-  const int pa0 = tid / NG, ta0 = tid - (tid / NG) * NG;
 
   issue(0);
   for (int c = 0; c < NCH; ++c) {
-    if (c + 1 < NCH) {
-      issue(c + 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    if (c + 1 < NCH) issue(c + 1);
+    if (!mbar_wait(bar0 + 8u * (uint32_t)(c & 1), (uint32_t)(c >> 1) & 1u)) s_fail = 1;
     __syncthreads();
+    if (s_fail) {                           // a copy never landed: wait (bounded) for the ones in flight, report
+      if (tid == 0) {
+        if (c + 1 < NCH) mbar_wait(bar0 + 8u * (uint32_t)((c + 1) & 1), (uint32_t)((c + 1) >> 1) & 1u);
+        mbar_wait(bar0 + 8u * (uint32_t)(c & 1), (uint32_t)(c >> 1) & 1u);
+        atomicCAS(status, 0, (int)BSE_ERR_TIMEOUT);
+      }
+      __syncthreads();
+      return;
+    }
     const int j1 = c / CPR, r0 = (c - j1 * CPR) * ROWS;
-    const float2* buf = ub + (size_t)(c & 1) * BMAX * ROWS * LD;
+    const float2* buf = ub + (size_t)(c & 1) * BMAX * BSTR;
 #pragma unroll
     for (int k1 = 0; k1 < K1; ++k1) {                           // stage 1: product + z FFT
       if (it1[k1] >= P * ROWS) continue;
       const int p = p1[k1], row = it1[k1] - p * ROWS;
       const int sa = sa1[k1], sb = sb1[k1];
-      const float4* xa = reinterpret_cast<const float4*>(buf + ((size_t)sa * ROWS + row) * LD);
-      const float4* xb = reinterpret_cast<const float4*>(buf + ((size_t)sb * ROWS + row) * LD);
+      const float4* xa = reinterpret_cast<const float4*>(buf + (size_t)sa * BSTR + (size_t)row * LD);
+      const float4* xb = reinterpret_cast<const float4*>(buf + (size_t)sb * BSTR + (size_t)row * LD);
       float2 x[N3];
 #pragma unroll
       for (int h = 0; h < N3 / 2; ++h) {
@@ -316,7 +368,7 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
         x[2 * h] = make_float2(va.x * vb.x + va.y * vb.y, va.x * vb.y - va.y * vb.x);          // conj(a) b
         x[2 * h + 1] = make_float2(va.z * vb.z + va.w * vb.w, va.z * vb.w - va.w * vb.z);
       }
-      fft::line<N3, true>(c_tw, x);
+      fft::line<N3, true>(x);
       float2* s1 = S1 + (size_t)p * S1P + (size_t)(r0 + row) * M3;
 #pragma unroll
       for (int f = -F3; f <= F3; ++f) s1[f + F3] = x[(f + N3) % N3];
@@ -328,46 +380,39 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
         float2 y[N2];
 #pragma unroll
         for (int j = 0; j < N2; ++j) y[j] = S1[(size_t)p * S1P + (size_t)j * M3 + m3];
-        fft::line<N2, true>(c_tw, y);
+        fft::line<N2, true>(y);
 #pragma unroll
         for (int f = -F2; f <= F2; ++f) S2[((size_t)p * M2 + (f + F2)) * M3 + m3] = y[(f + N2) % N2];
       }
       for (int g = tid; g < N1; g += THREADS) tw1[g] = fft::tw<N1, true>(c_tw, g * j1);
       __syncthreads();
-      {                                                          // stage 3: x DFT at sphere points
-        int p = pa0, t = ta0;
 #pragma unroll
-        for (int a = 0; a < ACC; ++a) {
-          if (p < P) {
-            const int2 g = sg[t];
-            const float2 s = S2[(size_t)p * M2 * M3 + g.y];
-            acc[a] = cadd(acc[a], cmul(s, tw1[g.x]));
-          }
-          t += THREADS;
-          while (t >= NG) {
-            t -= NG;
-            ++p;
-          }
+      for (int i = 0; i < PPT; ++i) {                            // stage 3: x DFT at this thread's sphere points
+        const int t = tid + i * THREADS;
+        if (t < NG) {
+          const int2 g = sg[t];
+          const float2 w = tw1[g.x];
+          const float2* s2 = S2 + g.y;
+#pragma unroll
+          for (int p = 0; p < PMAX; ++p)
+            if (p < P) acc[i * PMAX + p] = cadd(acc[i * PMAX + p], cmul(s2[p * M2 * M3], w));
         }
       }
     }
     __syncthreads();
   }
   const float inv = 1.0f / (float)(N1 * N2 * N3);
-  {
-    int p = pa0, t = ta0;
 #pragma unroll
-    for (int a = 0; a < ACC; ++a) {
+  for (int i = 0; i < PPT; ++i) {
+    const int t = tid + i * THREADS;
+    if (t >= NG) continue;
+#pragma unroll
+    for (int p = 0; p < PMAX; ++p) {
       if (p < P) {
         int sa, sb;
         float2* dst;
         product_of(d, jb, p, sa, sb, dst);
-        dst[t] = make_float2(acc[a].x * inv, acc[a].y * inv);
-      }
-      t += THREADS;
-      while (t >= NG) {
-        t -= NG;
-        ++p;
+        dst[t] = make_float2(acc[i * PMAX + p].x * inv, acc[i * PMAX + p].y * inv);
       }
     }
   }
@@ -402,10 +447,10 @@ __global__ void dipole_kernel(DevSys d, const float2* __restrict__ coef, const d
 
 // ---------------------------------------------------------------- dispatch
 typedef void (*RsFn)(DevSys, const float2*, float2*);
-typedef void (*PairFn)(DevSys, const float2*, float2*, int, int, int, long long);
+typedef void (*PairFn)(DevSys, const float2*, float2*, int, int, int, long long, int*, CUtensorMap);
 
 struct Variant {
-  int n1, n2, n3, f1, f2, f3, pmax, bmax, threads, acc;
+  int n1, n2, n3, f1, f2, f3, pmax, bmax, threads, ppt, rows;
   bool merged;
   RsFn rs;
   size_t rs_smem;
@@ -413,20 +458,20 @@ struct Variant {
   size_t (*pair_smem)(int);
 };
 
-#define BSE_VARIANT(N1, N2, N3, F1, F2, F3, PMAX, BMAX, ROWS, ACC, THREADS, MERGED)                              \
+#define BSE_VARIANT(N1, N2, N3, F1, F2, F3, PMAX, BMAX, ROWS, PPT, THREADS, MERGED)                              \
   Variant {                                                                                                      \
-    N1, N2, N3, F1, F2, F3, PMAX, BMAX, THREADS, ACC, MERGED, realspace_kernel<N1, N2, N3, F1, F2, F3>,          \
+    N1, N2, N3, F1, F2, F3, PMAX, BMAX, THREADS, PPT, ROWS, MERGED, realspace_kernel<N1, N2, N3, F1, F2, F3>,    \
         RsCfg<N1, N2, N3, F1, F2, F3>::smem,                                                                     \
-        pair_kernel<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, ACC, THREADS, MERGED>,                                 \
-        PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, ACC, THREADS, MERGED>::smem                                \
+        pair_kernel<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, PPT, THREADS, MERGED>,                                 \
+        PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, PPT, THREADS, MERGED>::smem                                \
   }
 
 const Variant kVariants[] = {
-    BSE_VARIANT(8, 8, 8, 2, 2, 2, 18, 12, 8, 8, 128, true),          // small test cells
-    BSE_VARIANT(24, 24, 24, 3, 3, 3, 18, 12, 24, 5, 448, true),      // fcc 4x4x4, 3v3c
-    BSE_VARIANT(32, 32, 32, 5, 5, 5, 25, 14, 16, 19, 416, true),     // fcc 8x8x8, 3v4c
-    BSE_VARIANT(48, 48, 48, 6, 6, 6, 16, 8, 16, 34, 256, false),     // fcc 12x12x12, 4v4c
-    BSE_VARIANT(12, 12, 48, 2, 2, 10, 18, 12, 12, 10, 224, true),    // hexagonal sheets, <= 3v3c
+    BSE_VARIANT(8, 8, 8, 2, 2, 2, 18, 12, 8, 1, 128, true),          // small test cells
+    BSE_VARIANT(24, 24, 24, 3, 3, 3, 18, 12, 24, 1, 448, true),      // fcc 4x4x4, 3v3c
+    BSE_VARIANT(32, 32, 32, 5, 5, 5, 25, 14, 16, 1, 416, true),      // fcc 8x8x8, 3v4c
+    BSE_VARIANT(48, 48, 48, 6, 6, 6, 16, 8, 16, 3, 256, false),      // fcc 12x12x12, 4v4c
+    BSE_VARIANT(12, 12, 48, 2, 2, 10, 18, 12, 12, 1, 224, true),     // hexagonal sheets, <= 3v3c
 };
 
 const Variant* pick(const DevSys& d) {
@@ -441,12 +486,33 @@ const Variant* pick(const DevSys& d) {
     const int px = d.nv * d.nc;
     const int pm = pd > px ? pd : px;
     ok = ok && pm <= v.pmax && bd <= v.bmax && d.nb <= v.bmax &&
-         (long long)pm * d.ng_max <= (long long)v.acc * v.threads;
+         d.ng_max <= v.ppt * v.threads;
     if (ok) return &v;
   }
   return nullptr;
 }
 
+
+// Tensor map of the u(r) workspace as a 2D array of z-lines ([Nk Nb N1 N2] lines x N3 complex,
+// 8-byte elements); boxes of (N3 + 2) x ROWS, out-of-bounds elements read as zero.
+static int make_tmap(const DevSys& d, const Variant* v, const void* u, CUtensorMap* tm) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    void* fp = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fp, 12000, cudaEnableDefault, &q) != cudaSuccess || !fp)
+      return (int)cudaErrorUnknown;
+    enc = (PFN_cuTensorMapEncodeTiled_v12000)fp;
+  }
+  cuuint64_t gdim[2] = {(cuuint64_t)d.n3, (cuuint64_t)d.nkpt * d.nb * d.n1 * d.n2};
+  cuuint64_t gstr[1] = {(cuuint64_t)d.n3 * 8};
+  cuuint32_t box[2] = {(cuuint32_t)(d.n3 + 2), (cuuint32_t)v->rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(u), gdim, gstr, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : (int)cudaErrorInvalidValue;
+}
 }  // namespace
 
 int upload_twiddles() {
@@ -466,17 +532,19 @@ int launch_realspace(const DevSys& d, const void* coef, void* u, void* stream) {
   return (int)cudaGetLastError();
 }
 
-int launch_pair_exchange(const DevSys& d, const void* u, void* rho_x, void* stream) {
+int launch_pair_exchange(const DevSys& d, const void* u, void* rho_x, int* status, void* stream) {
   const Variant* v = pick(d);
   if (!v) return (int)cudaErrorInvalidValue;
   const size_t sm = v->pair_smem(d.ng_max);
   cudaFuncSetAttribute((const void*)v->pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  v->pair<<<d.nkpt, v->threads, sm, (cudaStream_t)stream>>>(d, (const float2*)u, (float2*)rho_x, 0, 0, 0, 0);
+  CUtensorMap tm;
+  if (int e = make_tmap(d, v, u, &tm)) return e;
+  v->pair<<<d.nkpt, v->threads, sm, (cudaStream_t)stream>>>(d, (const float2*)u, (float2*)rho_x, 0, 0, 0, 0, status, tm);
   return (int)cudaGetLastError();
 }
 
 int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, int q_begin, int q_end, long long vbase,
-                       void* stream) {
+                       int* status, void* stream) {
   const Variant* v = pick(d);
   if (!v) return (int)cudaErrorInvalidValue;
   const size_t sm = v->pair_smem(d.ng_max);
@@ -485,8 +553,10 @@ int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, int q_begi
   const long long ntk = (d.nkpt + kTK - 1) / kTK, ntq = (nqc + kTQ - 1) / kTQ;
   const long long cells = ntq * ntk * kTQ * kTK * (v->merged ? 1 : 2);
   if (cells >= (1LL << 31)) return (int)cudaErrorInvalidValue;
+  CUtensorMap tm;
+  if (int e = make_tmap(d, v, u, &tm)) return e;
   v->pair<<<(unsigned)cells, v->threads, sm, (cudaStream_t)stream>>>(d, (const float2*)u, (float2*)rho_dir, 1,
-                                                                     q_begin, nqc, vbase);
+                                                                     q_begin, nqc, vbase, status, tm);
   return (int)cudaGetLastError();
 }
 

@@ -458,7 +458,7 @@ bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags, const void*
   }
   if (flags & BSE_PD_EXCHANGE) {
     if (!rho_x && !P) return set_error(BSE_ERR_ARG, "exchange stage needs rho_x or P");
-    if (rho_x && (st = cuda_check(launch_pair_exchange(d, ws, rho_x, stream), "pair exchange")) != BSE_OK) return st;
+    if (rho_x && (st = cuda_check(launch_pair_exchange(d, ws, rho_x, plan->d_status, stream), "pair exchange")) != BSE_OK) return st;
     if (P) {
       if (!coef || !energies) return set_error(BSE_ERR_ARG, "dipole needs coef and energies");
       if ((st = cuda_check(launch_dipole(d, coef, energies, sp.sys.gap_floor, P, stream), "dipole")) != BSE_OK)
@@ -468,7 +468,7 @@ bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags, const void*
   if (flags & BSE_PD_DIRECT) {
     if (!rho_dir || q_begin < 0 || q_end > d.nq || q_begin >= q_end) return set_error(BSE_ERR_ARG, "bad direct range");
     const long long vb = sp.qvec_off[q_begin];
-    if ((st = cuda_check(launch_pair_direct(d, ws, rho_dir, q_begin, q_end, vb, stream), "pair direct")) != BSE_OK)
+    if ((st = cuda_check(launch_pair_direct(d, ws, rho_dir, q_begin, q_end, vb, plan->d_status, stream), "pair direct")) != BSE_OK)
       return st;
   }
   return BSE_OK;
