@@ -315,7 +315,9 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
   const uint32_t ldst = smem_u32(ub) + (uint32_t)tid * kBand;
   __syncthreads();                          // barriers initialised, sphere table filled
 
+  bool alive = true;                        // false once one of this thread's waits gave up
   auto issue = [&](int c) {
+    if (!alive) return;
     const int j1 = c / CPR, r0 = (c - j1 * CPR) * ROWS;
     const uint32_t bar = bar0 + 8u * (uint32_t)(c & 1);
     if (tid == 0) mbar_expect_tx(bar, chunk_bytes);
@@ -327,6 +329,7 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
           : "memory");
     }
   };
+
   // stage-1 items of this thread (fixed for every chunk): line it = tid + k THREADS
   constexpr int K1 = (PMAX * ROWS + THREADS - 1) / THREADS;
   int it1[K1], p1[K1], sa1[K1], sb1[K1];
@@ -338,19 +341,15 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
     if (it1[k1] < P * ROWS) product_of(d, jb, p1[k1], sa1[k1], sb1[k1], dst_unused);
   }
 
+  // Barriers: a chunk that does not end a slab ends with one (its buffer is refilled next);
+  // a slab-end chunk has one before stage 2 and one before stage 3, which also order every
+  // thread's wait on a buffer's mbarrier before the next expect_tx on it.
   issue(0);
   for (int c = 0; c < NCH; ++c) {
     if (c + 1 < NCH) issue(c + 1);
-    if (!mbar_wait(bar0 + 8u * (uint32_t)(c & 1), (uint32_t)(c >> 1) & 1u)) s_fail = 1;
-    __syncthreads();
-    if (s_fail) {                           // a copy never landed: wait (bounded) for the ones in flight, report
-      if (tid == 0) {
-        if (c + 1 < NCH) mbar_wait(bar0 + 8u * (uint32_t)((c + 1) & 1), (uint32_t)((c + 1) >> 1) & 1u);
-        mbar_wait(bar0 + 8u * (uint32_t)(c & 1), (uint32_t)(c >> 1) & 1u);
-        atomicCAS(status, 0, (int)BSE_ERR_TIMEOUT);
-      }
-      __syncthreads();
-      return;
+    if (alive && !mbar_wait(bar0 + 8u * (uint32_t)(c & 1), (uint32_t)(c >> 1) & 1u)) {
+      alive = false;                        // a copy never landed: stop waiting and issuing, report below
+      s_fail = 1;
     }
     const int j1 = c / CPR, r0 = (c - j1 * CPR) * ROWS;
     const float2* buf = ub + (size_t)(c & 1) * BMAX * BSTR;
@@ -398,8 +397,18 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
             if (p < P) acc[i * PMAX + p] = cadd(acc[i * PMAX + p], cmul(s2[p * M2 * M3], w));
         }
       }
+    } else {
+      __syncthreads();
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  if (s_fail) {                             // bounded wait for copies still in flight, then report
+    if (tid == 0) {
+      if (NCH >= 2) mbar_wait(bar0 + 8u * (uint32_t)((NCH - 2) & 1), (uint32_t)((NCH - 2) >> 1) & 1u);
+      mbar_wait(bar0 + 8u * (uint32_t)((NCH - 1) & 1), (uint32_t)((NCH - 1) >> 1) & 1u);
+      atomicCAS(status, 0, (int)BSE_ERR_TIMEOUT);
+    }
+    return;
   }
   const float inv = 1.0f / (float)(N1 * N2 * N3);
 #pragma unroll
