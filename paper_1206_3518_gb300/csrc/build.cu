@@ -7,11 +7,11 @@
 // init_kernel   : 2K^x + diag on every tile that touches the upper block triangle; the
 //                 exchange scale sqrt(2 vbar/(Omega Nk)) is applied to both operands.
 // gemm_wr       : per q, X = W(q) R for the smaller band side (grouped over the q chunk),
-//                 stored as X^T rows [col][G] (G contiguous).
+//                 stored as X^T rows [col][G] (G contiguous); its own register-blocked tile.
 // block_kernel  : per upper block (k <= k'), M = X^H R of the other side (K = NG_q),
 //                 H_kk' = H_kk' - M/(Omega Nk) and the mirror H_k'k = H_kk'^H;
 //                 diagonal blocks become (B + B^H)/2.
-// All three GEMM-like steps use one tiled FP32 complex "NT" core: C[m][n] =
+// init_kernel uses the tiled FP32 complex "NT" core of gemm_tile.cuh: C[m][n] =
 // sum_k opA(A[m][k]) B[n][k] with both operands K-contiguous.
 #include <cuda_runtime.h>
 
@@ -58,28 +58,107 @@ __global__ __launch_bounds__(kGemmThreads) void init_kernel(DevSys d, const floa
 }
 
 // Grouped over the q chunk: X_q^T[col][G] = sum_G' R_q[col][G'] W_q[G][G']  (W Hermitian).
-__global__ __launch_bounds__(kGemmThreads) void gemm_wr(DevSys d, const float2* __restrict__ rho_dir,
-                                                       const float2* __restrict__ W, float2* __restrict__ X,
-                                                       int q_begin, long long vbase, int side_c) {
+// Tile 128 rows x 64 columns, K in steps of 16 complex; 256 threads, each 8 rows x 4 columns.
+// Operands are staged transposed ([k][row]) in shared memory so that a thread reads its 8
+// A values and 4 B values of one k with float4 loads; the next K step is prefetched into
+// registers while the current one is consumed (two shared buffers, one barrier per step).
+namespace wr {
+constexpr int TM = 128, TN = 64, TK = 16, kThreads = 256;
+struct Smem {                   // 48 KB: two K steps of both operands
+  float2 a[2][TK][TM];
+  float2 b[2][TK][TN];
+};
+}  // namespace wr
+
+__global__ __launch_bounds__(wr::kThreads, 2) void gemm_wr(DevSys d, const float2* __restrict__ rho_dir,
+                                                          const float2* __restrict__ W, float2* __restrict__ X,
+                                                          int q_begin, long long vbase, int side_c) {
+  using namespace wr;
   const int q = q_begin + blockIdx.z;
   const long long b0 = d.qblk_off[q_begin];
   const long long nblk = d.qblk_off[q + 1] - d.qblk_off[q];
   const int w = side_c ? d.nc * d.nc : d.nv * d.nv;
   const int M = (int)(nblk * w), NG = d.ngq[q];
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
   if (m0 >= M || n0 >= NG) return;
   long long aoff = d.qvec_off[q] - vbase;
   if (side_c) aoff += nblk * d.nv * d.nv;
   const float2* A = rho_dir + (size_t)aoff * d.ng_max;
   const float2* B = W + (size_t)q * d.ng_max * d.ng_max;
   float2* C = X + (size_t)((d.qblk_off[q] - b0) * w) * d.ng_max;
-  __shared__ gemm::Smem sm;
-  float2 acc[4][4];
-  gemm::tile<true, true, false, false>(A, d.ng_max, M, B, d.ng_max, NG, NG, m0, n0, sm, acc);
-  const int tm = threadIdx.x / 16, tn = threadIdx.x % 16;
+  __shared__ __align__(16) Smem sm;
+  const int t = threadIdx.x;
+  const int tm = t / 16, tn = t % 16;
+  // staging assignment: A row t/2, K half t%2 (8 values); B row t/4, K quarter t%4 (4 values)
+  const int ar = t >> 1, ah = (t & 1) * 8, br = t >> 2, bq = (t & 3) * 4;
+  const bool a_in = m0 + ar < M, b_in = n0 + br < NG;
+  const float2* Ap = A + (size_t)(m0 + ar) * d.ng_max;
+  const float2* Bp = B + (size_t)(n0 + br) * d.ng_max;
+  float2 ra[8], rb[4];
+  auto fetch = [&](int k0) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = m0 + tm * 4 + i;
+    for (int i = 0; i < 8; ++i) {
+      const int k = k0 + ah + i;
+      ra[i] = (a_in && k < NG) ? Ap[k] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = k0 + bq + i;
+      rb[i] = (b_in && k < NG) ? Bp[k] : make_float2(0.f, 0.f);
+    }
+  };
+  auto put = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sm.a[buf][ah + i][ar] = ra[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sm.b[buf][bq + i][br] = rb[i];
+  };
+  float2 acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  fetch(0);
+  put(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < NG; k0 += TK) {
+    const bool more = k0 + TK < NG;
+    if (more) fetch(k0 + TK);
+#pragma unroll
+    for (int k = 0; k < TK; ++k) {
+      float2 av[8], bv[4];
+      const float4* pa = reinterpret_cast<const float4*>(&sm.a[buf][k][tm * 8]);
+      const float4* pb = reinterpret_cast<const float4*>(&sm.b[buf][k][tn * 4]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 v = pa[i];
+        av[2 * i] = make_float2(v.x, v.y);
+        av[2 * i + 1] = make_float2(v.z, v.w);
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const float4 v = pb[j];
+        bv[2 * j] = make_float2(v.x, v.y);
+        bv[2 * j + 1] = make_float2(v.z, v.w);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fmaf(av[i].x, bv[j].x, fmaf(-av[i].y, bv[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(av[i].x, bv[j].y, fmaf(av[i].y, bv[j].x, acc[i][j].y));
+        }
+    }
+    if (more) {
+      put(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = m0 + tm * 8 + i;
     if (r >= M) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -186,8 +265,8 @@ int launch_kernel_init(const DevSys& d, const void* rho_x, const double* energie
 
 int launch_gemm_wr(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long vbase, long long max_rows,
                    const void* W, void* X, int side_c, void* stream) {
-  dim3 grid((d.ng_max + BN - 1) / BN, (unsigned)((max_rows + BM - 1) / BM), q_end - q_begin);
-  gemm_wr<<<grid, kGemmThreads, 0, (cudaStream_t)stream>>>(d, (const float2*)rho_dir, (const float2*)W, (float2*)X,
+  dim3 grid((d.ng_max + wr::TN - 1) / wr::TN, (unsigned)((max_rows + wr::TM - 1) / wr::TM), q_end - q_begin);
+  gemm_wr<<<grid, wr::kThreads, 0, (cudaStream_t)stream>>>(d, (const float2*)rho_dir, (const float2*)W, (float2*)X,
                                                           q_begin, vbase, side_c);
   return (int)cudaGetLastError();
 }
@@ -202,8 +281,8 @@ int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin
     void* split_ws = (char*)ws + x_bytes(d, q_end - q_begin);
     e = launch_gemm_wr_tc(d, rho_dir, q_begin, q_end, vbase, max_rows, W, ws, split_ws, side_c, status, stream);
   } else if (prec == BSE_PREC_FP32) {
-    dim3 grid((d.ng_max + BN - 1) / BN, (unsigned)((max_rows + BM - 1) / BM), q_end - q_begin);
-    gemm_wr<<<grid, kGemmThreads, 0, st>>>(d, (const float2*)rho_dir, (const float2*)W, (float2*)ws, q_begin, vbase,
+    dim3 grid((d.ng_max + wr::TN - 1) / wr::TN, (unsigned)((max_rows + wr::TM - 1) / wr::TM), q_end - q_begin);
+    gemm_wr<<<grid, wr::kThreads, 0, st>>>(d, (const float2*)rho_dir, (const float2*)W, (float2*)ws, q_begin, vbase,
                                            side_c);
     e = (int)cudaGetLastError();
   } else {
