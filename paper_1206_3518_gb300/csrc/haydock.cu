@@ -314,14 +314,14 @@ struct HayArgs {
 };
 
 // hpart[cta][i] = sum over own rows conj(V[i][r]) w[r], i in [0, n) (double-float products).
+// One thread per basis vector walks the CTA's rows with independent, unrolled loads (the rows of
+// V owned by a CTA are written and read by that CTA only, so plain cached loads are coherent).
 __device__ void project_partial(const HayArgs& A, const float4* wsm, int row0, int nrows, int n) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int dim = A.dim;
-  for (int i = warp; i < n; i += kWarps) {
+  for (int i = threadIdx.x; i < n; i += kThreads) {
     const float4* Vi = A.V + (size_t)i * dim + row0;
     float2 sr = make_float2(0.f, 0.f), si = make_float2(0.f, 0.f);
-    for (int r = lane; r < nrows; r += 32) {
-      const float4 v = __ldcg(Vi + r), w = wsm[r];
+    auto mac = [&](float4 v, float4 w) {
       const float2 vr = make_float2(v.x, v.y), vi = make_float2(v.z, v.w);
       const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
       // conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr)
@@ -329,9 +329,17 @@ __device__ void project_partial(const HayArgs& A, const float4* wsm, int row0, i
       df_mac(sr, vi, wi);
       df_mac(si, vr, wi);
       df_mac(si, df_neg(vi), wr);
+    };
+    int r = 0;
+    for (; r + 4 <= nrows; r += 4) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = Vi[r + u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) mac(v[u], wsm[r + u]);
     }
-    const float4 t = cdf_warp_sum(make_float4(sr.x, sr.y, si.x, si.y));
-    if (lane == 0) A.hpart[(size_t)A.grank * A.nsteps + i] = cdf_val(t);
+    for (; r < nrows; ++r) mac(Vi[r], wsm[r]);
+    A.hpart[(size_t)A.grank * A.nsteps + i] = cdf_val(make_float4(sr.x, sr.y, si.x, si.y));
   }
 }
 
@@ -350,20 +358,21 @@ __device__ void reduce_coeffs(const HayArgs& A, double2* h, int n) {
   }
 }
 
-// w[r] -= sum_i V[i][r] h[i] over own rows; warps split i, lanes split rows; h staged split in hs.
-__device__ void subtract_projection(const HayArgs& A, float4* wsm, float4 (*red)[32], float4* hs, const double2* h,
+// w[r] -= sum_i V[i][r] h[i] over own rows.  Threads are (vector group, row) with rows fastest:
+// each sums every ng-th basis vector for its row with independent, unrolled loads, then the
+// ng partials of a row are added in a fixed order.  h is staged split (hi, lo) in hs.
+__device__ void subtract_projection(const HayArgs& A, float4* wsm, float4* red, float4* hs, const double2* h,
                                     int row0, int nrows, int n) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int dim = A.dim;
   for (int i = threadIdx.x; i < n; i += kThreads) hs[i] = cdf_split(__ldcg(h + i));
   __syncthreads();
-  for (int r0 = 0; r0 < nrows; r0 += 32) {
-    const int r = r0 + lane;
-    float2 sr = make_float2(0.f, 0.f), si = make_float2(0.f, 0.f);
-    if (r < nrows) {
-      for (int i = warp; i < n; i += kWarps) {
-        const float4 v = __ldcg(A.V + (size_t)i * dim + row0 + r);
-        const float4 c = hs[i];
+  for (int rb = 0; rb < nrows; rb += kThreads) {
+    const int nr = min(nrows - rb, kThreads);
+    const int ng = kThreads / nr;
+    const int r = threadIdx.x % nr, ig = threadIdx.x / nr;
+    if (ig < ng) {
+      float2 sr = make_float2(0.f, 0.f), si = make_float2(0.f, 0.f);
+      auto mac = [&](float4 v, float4 c) {
         const float2 vr = make_float2(v.x, v.y), vi = make_float2(v.z, v.w);
         const float2 cr = make_float2(c.x, c.y), ci = make_float2(c.z, c.w);
         // v c = (vr cr - vi ci) + i (vr ci + vi cr)
@@ -371,24 +380,34 @@ __device__ void subtract_projection(const HayArgs& A, float4* wsm, float4 (*red)
         df_mac(sr, df_neg(vi), ci);
         df_mac(si, vr, ci);
         df_mac(si, vi, cr);
-      }
-    }
-    red[warp][lane] = make_float4(sr.x, sr.y, si.x, si.y);
-    __syncthreads();
-    if (warp == 0 && r < nrows) {
-      float2 tr = make_float2(0.f, 0.f), ti = make_float2(0.f, 0.f);
+      };
+      const float4* Vr = A.V + row0 + rb + r;
+      int i = ig;
+      for (; i + 3 * ng < n; i += 4 * ng) {
+        float4 v[4];
 #pragma unroll
-      for (int q = 0; q < kWarps; ++q) {
-        df_add(tr, make_float2(red[q][lane].x, red[q][lane].y));
-        df_add(ti, make_float2(red[q][lane].z, red[q][lane].w));
+        for (int u = 0; u < 4; ++u) v[u] = Vr[(size_t)(i + u * ng) * dim];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) mac(v[u], hs[i + u * ng]);
       }
-      const float4 w = wsm[r];
+      for (; i < n; i += ng) mac(Vr[(size_t)i * dim], hs[i]);
+      red[ig * nr + r] = make_float4(sr.x, sr.y, si.x, si.y);
+    }
+    __syncthreads();
+    if (threadIdx.x < nr) {
+      float2 tr = make_float2(0.f, 0.f), ti = make_float2(0.f, 0.f);
+      for (int q = 0; q < ng; ++q) {
+        const float4 t = red[q * nr + threadIdx.x];
+        df_add(tr, make_float2(t.x, t.y));
+        df_add(ti, make_float2(t.z, t.w));
+      }
+      const float4 w = wsm[rb + threadIdx.x];
       float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
       df_add(wr, df_neg(tr));
       df_add(wi, df_neg(ti));
       wr = df_norm(wr);
       wi = df_norm(wi);
-      wsm[r] = make_float4(wr.x, wr.y, wi.x, wi.y);
+      wsm[rb + threadIdx.x] = make_float4(wr.x, wr.y, wi.x, wi.y);
     }
     __syncthreads();
   }
@@ -478,7 +497,7 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(const __grid_const
   float4* wsm = dyn;                                // own rows of w (double-float)
   float4* hs = dyn + B.rows_max;                    // projection coefficients (double-float)
   float2* xs = reinterpret_cast<float2*>(hs + B.nsteps);   // column tile of v_j (FP32)
-  __shared__ float4 red[kWarps][32];
+  __shared__ float4 red[kThreads];
   __shared__ double red1[kWarps];
   const int dim = A.dim;
   const int rows_per = (dim + A.gsize - 1) / A.gsize;
@@ -506,13 +525,17 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(const __grid_const
   if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
 
   int done = A.nsteps;
+  float vscale = 1.0f;                      // vf holds v_j / vscale: w_j unnormalised, scaled when staged
   for (int j = 0; j < A.nsteps; ++j) {
     // w = H v_j on own rows: v_j staged in shared memory in column tiles, H streamed once
     for (int r = threadIdx.x; r < nrows; r += kThreads) wsm[r] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int col0 = 0; col0 < dim; col0 += kXTile) {
       const int cols = min(kXTile, dim - col0);
       __syncthreads();
-      for (int c = threadIdx.x; c < cols; c += kThreads) xs[c] = __ldcg(A.vf + col0 + c);
+      for (int c = threadIdx.x; c < cols; c += kThreads) {
+        const float2 x = __ldcg(A.vf + col0 + c);
+        xs[c] = make_float2(x.x * vscale, x.y * vscale);
+      }
       __syncthreads();
       for (int r = warp; r < nrows; r += kWarps) {
         float2 ar = make_float2(0.f, 0.f), ai = make_float2(0.f, 0.f);
@@ -552,6 +575,7 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(const __grid_const
     for (int r = threadIdx.x; r < nrows; r += kThreads) {
       const double2 w = cdf_val(wsm[r]);
       ww += w.x * w.x + w.y * w.y;
+      A.vf[row0 + r] = make_float2((float)w.x, (float)w.y);   // published unnormalised
     }
     ww = block_sum(ww, red1);
     if (threadIdx.x == 0) A.npart[2 * A.grank] = ww;
@@ -574,14 +598,12 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(const __grid_const
       break;
     }
     const double binv = 1.0 / bn;
-    float4* Vn = A.V + (size_t)(j + 1) * dim + row0;
+    float4* Vn = A.V + (size_t)(j + 1) * dim + row0;   // own rows only: no grid barrier needed
     for (int r = threadIdx.x; r < nrows; r += kThreads) {
       const double2 w = cdf_val(wsm[r]);
-      const double2 v = make_double2(w.x * binv, w.y * binv);
-      Vn[r] = cdf_split(v);
-      A.vf[row0 + r] = make_float2((float)v.x, (float)v.y);
+      Vn[r] = cdf_split(make_double2(w.x * binv, w.y * binv));
     }
-    if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
+    vscale = (float)binv;
   }
   if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
   if (A.grank == 0 && threadIdx.x == 0) *A.steps_done = done;
