@@ -269,6 +269,42 @@ bse_status bse_spectrum_backward(bse_plan* plan, int s, const void* H, const voi
                                  void* dL_drho_dir, void* dL_dW,
                                  void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * Tile-shape variants of the pair-density kernel (step A2) and their autotuner.
+ *
+ * Several pair-kernel variants are compiled per real-space grid (threads per CTA, z-lines per
+ * chunk, maximum band products and band slabs per CTA, sphere points per thread, vv'/cc'
+ * merged in one CTA or not).  A system runs the variant selected for it, by default the
+ * first one valid for its grid, band counts and spheres.  No counterpart in the paper.
+ *
+ * bse_pair_variants lists the valid variants of system s (up to cap entries of out, the
+ * total in *count) and the index in use (*current).  bse_set_pair_variant selects one by its
+ * index (-1 restores the default); BSE_ERR_ARG if the index is not valid for the system.
+ * bse_autotune_pair times every valid variant on the direct pair densities of q in
+ * [q_begin, q_end) (one warm-up launch, then reps timed launches each, CUDA events on stream),
+ * writes the mean milliseconds per launch to ms[i] (i < cap, in bse_pair_variants order),
+ * selects the fastest and returns its index in *chosen.  It needs the pair workspace of
+ * bse_pair_densities (its contents only feed the timed launches) and rho_dir with room for
+ * bse_rho_dir_count(q_begin, q_end) vectors, whose contents it overwrites.  It synchronises
+ * the stream (not capturable).  Errors: BSE_ERR_ARG, BSE_ERR_WORKSPACE, BSE_ERR_UNSUPPORTED,
+ * BSE_ERR_CUDA (the previous selection is kept).
+ */
+typedef struct {
+  int index;              /* variant id (argument of bse_set_pair_variant) */
+  int threads;            /* threads per CTA */
+  int rows;               /* z-lines per pipelined chunk */
+  int max_products;       /* band products per CTA */
+  int max_bands;          /* band slabs per CTA */
+  int points_per_thread;  /* sphere points accumulated per thread */
+  int merged;             /* 1: vv' and cc' products of a block in one CTA */
+} bse_pair_variant;
+
+bse_status bse_pair_variants(const bse_plan* plan, int s, bse_pair_variant* out, int cap, int* count,
+                             int* current);
+bse_status bse_set_pair_variant(bse_plan* plan, int s, int index);
+bse_status bse_autotune_pair(bse_plan* plan, int s, void* ws, size_t ws_bytes, void* rho_dir, int q_begin,
+                             int q_end, int reps, float* ms, int cap, int* chosen, void* stream);
+
 /* Synchronise the stream and return (then clear) the plan's device status word. */
 bse_status bse_status_read(bse_plan* plan, void* stream);
 

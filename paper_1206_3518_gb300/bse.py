@@ -27,6 +27,7 @@ EXPORTED = [
     "bse_last_error", "bse_plan_create", "bse_plan_create_host", "bse_plan_destroy", "bse_plan_info", "bse_gvectors",
     "bse_pair_blocks", "bse_workspace_size", "bse_rho_dir_count", "bse_pair_densities",
     "bse_build_kernel", "bse_apply_H", "bse_spectrum", "bse_spectrum_static", "bse_spectrum_batch", "bse_spectrum_backward", "bse_status_read",
+    "bse_pair_variants", "bse_set_pair_variant", "bse_autotune_pair",
 ]
 
 
@@ -42,6 +43,12 @@ class BseInfo(ctypes.Structure):
                 ("npw_max", ctypes.c_int), ("ng_max", ctypes.c_int), ("ng0", ctypes.c_int),
                 ("nq", ctypes.c_int), ("nblocks", ctypes.c_longlong), ("omega_cell", ctypes.c_double),
                 ("norm", ctypes.c_double), ("prefactor", ctypes.c_double)]
+
+
+class BsePairVariant(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_int), ("threads", ctypes.c_int), ("rows", ctypes.c_int),
+                ("max_products", ctypes.c_int), ("max_bands", ctypes.c_int), ("points_per_thread", ctypes.c_int),
+                ("merged", ctypes.c_int)]
 
 
 class BseError(RuntimeError):
@@ -82,6 +89,10 @@ def load():
                                        ctypes.POINTER(sz), vp]
     lib.bse_spectrum_backward.argtypes = [vp, i, vp, vp, i, vp, i, d, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.bse_status_read.argtypes = [vp, vp]
+    lib.bse_pair_variants.argtypes = [vp, i, ctypes.POINTER(BsePairVariant), i, ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.bse_set_pair_variant.argtypes = [vp, i, i]
+    lib.bse_autotune_pair.argtypes = [vp, i, vp, sz, vp, i, i, i, ctypes.POINTER(ctypes.c_float), i,
+                                      ctypes.POINTER(i), vp]
     for name in EXPORTED:
         if name != "bse_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -248,3 +259,29 @@ def bse_spectrum_backward(plan, s, H, P, nsteps, omega, eta, dL_deps2, rho_x, rh
 
 def bse_status_read(plan):
     _check(load().bse_status_read(plan.handle, _stream()))
+
+
+def bse_pair_variants(plan, s):
+    """Valid pair-kernel variants of system s (list of dicts) and the index in use."""
+    lib = load()
+    arr = (BsePairVariant * 64)()
+    n, cur = ctypes.c_int(), ctypes.c_int()
+    _check(lib.bse_pair_variants(plan.handle, s, arr, 64, ctypes.byref(n), ctypes.byref(cur)))
+    out = [{f: getattr(arr[k], f) for f, _ in BsePairVariant._fields_} for k in range(min(n.value, 64))]
+    return out, cur.value
+
+
+def bse_set_pair_variant(plan, s, index):
+    _check(load().bse_set_pair_variant(plan.handle, s, int(index)))
+
+
+def bse_autotune_pair(plan, s, ws, rho_dir, q_begin, q_end, reps=3):
+    """Times every valid variant on the direct pair densities of [q_begin, q_end), selects the fastest.
+
+    Returns (ms per launch in bse_pair_variants order, chosen index)."""
+    ms = (ctypes.c_float * 64)()
+    chosen = ctypes.c_int()
+    _check(load().bse_autotune_pair(plan.handle, s, _ptr(ws), _nbytes(ws), _ptr(rho_dir), q_begin, q_end, int(reps),
+                                    ms, 64, ctypes.byref(chosen), _stream()))
+    n = len(bse_pair_variants(plan, s)[0])
+    return [float(ms[k]) for k in range(n)], chosen.value

@@ -30,6 +30,7 @@ struct DevSys {
   const double* kgq;              // [nkpt][npw_max] qhat.(k+G), Cartesian
   const float* xscale;            // [ng_max] sqrt(2 vbar(G) / (Omega Nk)), 0 at G = 0 and beyond ng0
   long long nblocks;
+  int pair_variant;               // index of the pair-kernel variant chosen for this system, -1 = first valid
 };
 
 struct SysPlan {
@@ -60,6 +61,10 @@ int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, int q_begi
                        int* status, void* stream);
 int launch_dipole(const DevSys& d, const void* coef, const double* energies, double gap_floor, void* P, void* stream);
 int pair_supported(const DevSys& d);
+// Pair-kernel variants compiled for this system: writes up to cap (index, threads, rows, pmax, bmax, ppt,
+// merged) septets, returns the number valid; pair_variant_current returns the index pick() uses.
+int pair_variants(const DevSys& d, int* out, int cap);
+int pair_variant_current(const DevSys& d);
 
 int launch_kernel_init(const DevSys& d, const void* rho_x, const double* energies, double delta, void* H, void* stream);
 int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long b_begin,

@@ -475,32 +475,41 @@ struct Variant {
         PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, PPT, THREADS, MERGED>::smem                                \
   }
 
+// Candidate tile shapes per grid; the planner takes the first valid one unless a variant was chosen
+// (by the autotuner or the caller).  The hexagonal-sheet grid has variants sized for 2-5, 8-10 and
+// 18 band products, the fcc 8x8x8 grid two chunk heights.
 const Variant kVariants[] = {
     BSE_VARIANT(8, 8, 8, 2, 2, 2, 18, 12, 8, 1, 128, true),          // small test cells
     BSE_VARIANT(24, 24, 24, 3, 3, 3, 18, 12, 24, 1, 448, true),      // fcc 4x4x4, 3v3c
     BSE_VARIANT(32, 32, 32, 5, 5, 5, 25, 14, 16, 1, 416, true),      // fcc 8x8x8, 3v4c
+    BSE_VARIANT(32, 32, 32, 5, 5, 5, 25, 14, 8, 2, 224, true),       //   half-height chunks
     BSE_VARIANT(48, 48, 48, 6, 6, 6, 16, 8, 16, 3, 256, false),      // fcc 12x12x12, 4v4c
     BSE_VARIANT(12, 12, 48, 2, 2, 10, 18, 12, 12, 1, 224, true),     // hexagonal sheets, <= 3v3c
+    BSE_VARIANT(12, 12, 48, 2, 2, 10, 10, 8, 12, 1, 128, true),      //   <= 10 products, <= 4 bands
+    BSE_VARIANT(12, 12, 48, 2, 2, 10, 5, 6, 12, 2, 64, true),        //   1v2c, 2v1c, 1v1c
 };
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
-const Variant* pick(const DevSys& d) {
+bool valid_for(const Variant& v, const DevSys& d) {
+  if (v.n1 != d.n1 || v.n2 != d.n2 || v.n3 != d.n3) return false;
   const int vmax = d.nv > d.nc ? d.nv : d.nc;
-  for (const Variant& v : kVariants) {
-    if (v.n1 != d.n1 || v.n2 != d.n2 || v.n3 != d.n3) continue;
-    const int f[3] = {v.f1, v.f2, v.f3};
-    bool ok = true;
-    for (int j = 0; j < 3; ++j) ok = ok && d.fwf[j] <= f[j] && d.fpair[j] <= f[j];
-    const int pd = v.merged ? d.nv * d.nv + d.nc * d.nc : vmax * vmax;
-    const int bd = v.merged ? 2 * d.nb : 2 * vmax;
-    const int px = d.nv * d.nc;
-    const int pm = pd > px ? pd : px;
-    ok = ok && pm <= v.pmax && bd <= v.bmax && d.nb <= v.bmax &&
-         d.ng_max <= v.ppt * v.threads;
-    if (ok) return &v;
-  }
-  return nullptr;
+  const int f[3] = {v.f1, v.f2, v.f3};
+  bool ok = true;
+  for (int j = 0; j < 3; ++j) ok = ok && d.fwf[j] <= f[j] && d.fpair[j] <= f[j];
+  const int pd = v.merged ? d.nv * d.nv + d.nc * d.nc : vmax * vmax;
+  const int bd = v.merged ? 2 * d.nb : 2 * vmax;
+  const int px = d.nv * d.nc;
+  const int pm = pd > px ? pd : px;
+  return ok && pm <= v.pmax && bd <= v.bmax && d.nb <= v.bmax && d.ng_max <= v.ppt * v.threads;
 }
 
+const Variant* pick(const DevSys& d) {
+  if (d.pair_variant >= 0 && d.pair_variant < kNumVariants && valid_for(kVariants[d.pair_variant], d))
+    return &kVariants[d.pair_variant];
+  for (const Variant& v : kVariants)
+    if (valid_for(v, d)) return &v;
+  return nullptr;
+}
 
 // Tensor map of the u(r) workspace as a 2D array of z-lines ([Nk Nb N1 N2] lines x N3 complex,
 // 8-byte elements); boxes of (N3 + 2) x ROWS, out-of-bounds elements read as zero.
@@ -532,6 +541,31 @@ int upload_twiddles() {
 }
 
 int pair_supported(const DevSys& d) { return pick(d) != nullptr; }
+
+int pair_variants(const DevSys& d, int* out, int cap) {
+  int n = 0;
+  for (int i = 0; i < kNumVariants; ++i) {
+    const Variant& v = kVariants[i];
+    if (!valid_for(v, d)) continue;
+    if (out && n < cap) {
+      int* o = out + 7 * n;
+      o[0] = i;
+      o[1] = v.threads;
+      o[2] = v.rows;
+      o[3] = v.pmax;
+      o[4] = v.bmax;
+      o[5] = v.ppt;
+      o[6] = v.merged ? 1 : 0;
+    }
+    ++n;
+  }
+  return n;
+}
+
+int pair_variant_current(const DevSys& d) {
+  const Variant* v = pick(d);
+  return v ? (int)(v - kVariants) : -1;
+}
 
 int launch_realspace(const DevSys& d, const void* coef, void* u, void* stream) {
   const Variant* v = pick(d);

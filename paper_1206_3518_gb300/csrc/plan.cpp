@@ -137,6 +137,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   d.n1 = s.fft[0];
   d.n2 = s.fft[1];
   d.n3 = s.fft[2];
+  d.pair_variant = -1;
   d.nk1 = nk1;
   d.nk2 = nk2;
   d.nk3 = nk3;
@@ -472,6 +473,88 @@ bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags, const void*
       return st;
   }
   return BSE_OK;
+}
+
+bse_status bse_pair_variants(const bse_plan* plan, int s, bse_pair_variant* out, int cap, int* count, int* current) {
+  bse_status st = check_plan(plan, s);
+  if (st != BSE_OK) return st;
+  if (!count || !current || cap < 0 || (cap > 0 && !out)) return set_error(BSE_ERR_ARG, "bad output arguments");
+  const DevSys& d = plan->sys[s].d;
+  int buf[7 * 64];
+  const int n = pair_variants(d, buf, 64);
+  for (int i = 0; i < n && i < cap && i < 64; ++i) {
+    const int* b = buf + 7 * i;
+    out[i] = bse_pair_variant{b[0], b[1], b[2], b[3], b[4], b[5], b[6]};
+  }
+  *count = n;
+  *current = pair_variant_current(d);
+  return BSE_OK;
+}
+
+bse_status bse_set_pair_variant(bse_plan* plan, int s, int index) {
+  bse_status st = check_plan(plan, s);
+  if (st != BSE_OK) return st;
+  DevSys& d = plan->sys[s].d;
+  if (index != -1) {
+    int buf[7 * 64];
+    const int n = pair_variants(d, buf, 64);
+    bool found = false;
+    for (int i = 0; i < n && i < 64; ++i) found = found || buf[7 * i] == index;
+    if (!found) return set_error(BSE_ERR_ARG, "pair variant not valid for this system");
+  }
+  d.pair_variant = index;
+  return BSE_OK;
+}
+
+bse_status bse_autotune_pair(bse_plan* plan, int s, void* ws, size_t ws_bytes, void* rho_dir, int q_begin, int q_end,
+                             int reps, float* ms, int cap, int* chosen, void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  SysPlan& sp = plan->sys[s];
+  DevSys& d = sp.d;
+  size_t need = 0;
+  bse_workspace_size(plan, s, BSE_WS_PAIR, 0, &need);
+  if (!ws || ws_bytes < need) return set_error(BSE_ERR_WORKSPACE, "pair workspace too small");
+  if (!rho_dir || q_begin < 0 || q_end > d.nq || q_begin >= q_end || reps < 1 || !chosen || cap < 0 ||
+      (cap > 0 && !ms))
+    return set_error(BSE_ERR_ARG, "bad autotune arguments");
+  int buf[7 * 64];
+  const int n = pair_variants(d, buf, 64);
+  if (n == 0) return set_error(BSE_ERR_UNSUPPORTED, "no pair-FFT kernel compiled for this grid/sphere");
+  cudaStream_t stm = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if ((st = cuda_check(cudaEventCreate(&e0), "event")) != BSE_OK) return st;
+  if ((st = cuda_check(cudaEventCreate(&e1), "event")) != BSE_OK) {
+    cudaEventDestroy(e0);
+    return st;
+  }
+  const int saved = d.pair_variant;
+  const long long vb = sp.qvec_off[q_begin];
+  float best = 0.f;
+  int besti = -1;
+  for (int i = 0; i < n && i < 64 && st == BSE_OK; ++i) {
+    d.pair_variant = buf[7 * i];
+    st = cuda_check(launch_pair_direct(d, ws, rho_dir, q_begin, q_end, vb, plan->d_status, stream), "autotune warm-up");
+    if (st != BSE_OK) break;
+    cudaEventRecord(e0, stm);
+    for (int r = 0; r < reps && st == BSE_OK; ++r)
+      st = cuda_check(launch_pair_direct(d, ws, rho_dir, q_begin, q_end, vb, plan->d_status, stream), "autotune");
+    cudaEventRecord(e1, stm);
+    if (st == BSE_OK) st = cuda_check(cudaEventSynchronize(e1), "autotune sync");
+    float t = 0.f;
+    if (st == BSE_OK) st = cuda_check(cudaEventElapsedTime(&t, e0, e1), "autotune timing");
+    t /= (float)reps;
+    if (i < cap) ms[i] = t;
+    if (st == BSE_OK && (besti < 0 || t < best)) {
+      best = t;
+      besti = buf[7 * i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  d.pair_variant = (st == BSE_OK) ? besti : saved;
+  *chosen = d.pair_variant;
+  return st;
 }
 
 bse_status bse_build_kernel(bse_plan* plan, int s, unsigned flags, const void* rho_x, const void* rho_dir,
