@@ -32,6 +32,7 @@ constexpr int kThreads = 512, kWarps = kThreads / 32;
 constexpr int kMaxGrid = 1024;
 constexpr double kBreakdownRel = 1e-10;
 constexpr int kXTile = 8192;          // columns of v_j staged in shared memory per pass (64 KB)
+constexpr size_t kDynMax = 150 * 1024;   // dynamic shared memory budget: the rest stays L1 for the H stream
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -39,37 +40,53 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
-// Barrier over the gsize CTAs of one system's group, on a (count, generation) pair; false if
-// the wait timed out or another CTA already reported an error.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Barrier over the gsize CTAs of one system's group, on a (count, generation) pair: arrivals are
+// acquire-release atomics, the last arrival resets the count and releases the generation, the
+// others poll it with acquire loads.  False if the wait timed out or another CTA already
+// reported an error.
 __device__ bool grid_barrier(unsigned* bar, int* status, unsigned gsize) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
+    unsigned* gen = bar + 1;
+    const unsigned g = ld_acquire(gen);
+    const unsigned arrived = atom_add_acq_rel(bar, 1u);
     int good = 1;
     if (arrived == gsize - 1) {
       atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
+      red_add_release(gen, 1u);
     } else {
       const unsigned long long t0 = globaltimer();
-      while (*gen == g) {
-        if (*(volatile int*)status != 0) {
-          good = 0;
-          break;
+      unsigned it = 0;
+      while (ld_acquire(gen) == g) {
+        __nanosleep(32);
+        if ((++it & 31u) == 0) {
+          if (*(volatile int*)status != 0) {
+            good = 0;
+            break;
+          }
+          if (globaltimer() - t0 > 2000000000ull) {
+            atomicCAS(status, 0, (int)BSE_ERR_TIMEOUT);
+            good = 0;
+            break;
+          }
         }
-        if (globaltimer() - t0 > 2000000000ull) {
-          atomicCAS(status, 0, (int)BSE_ERR_TIMEOUT);
-          good = 0;
-          break;
-        }
-        __nanosleep(100);
       }
     }
-    __threadfence();
     ok = good;
   }
   __syncthreads();
@@ -316,19 +333,30 @@ struct HayArgs {
 // hpart[cta][i] = sum over own rows conj(V[i][r]) w[r], i in [0, n) (double-float products).
 // One thread per basis vector walks the CTA's rows with independent, unrolled loads (the rows of
 // V owned by a CTA are written and read by that CTA only, so plain cached loads are coherent).
-__device__ void project_partial(const HayArgs& A, const float4* wsm, int row0, int nrows, int n) {
-  const int dim = A.dim;
+// This CTA's rows of basis vector i: the shared copy for i < vsk (row stride vrows), else global.
+struct BasisRows {
+  const float4* sm;     // [vsk][vrows]
+  const float4* gl;     // V + row0, row stride dim
+  int vsk, vrows, dim;
+  __device__ __forceinline__ const float4* row(int i) const {
+    return i < vsk ? sm + (size_t)i * vrows : gl + (size_t)i * dim;
+  }
+};
+
+__device__ void project_partial(const HayArgs& A, const BasisRows& Vb, const float4* wsm, int nrows, int n) {
   for (int i = threadIdx.x; i < n; i += kThreads) {
-    const float4* Vi = A.V + (size_t)i * dim + row0;
-    float2 sr = make_float2(0.f, 0.f), si = make_float2(0.f, 0.f);
-    auto mac = [&](float4 v, float4 w) {
+    const float4* Vi = Vb.row(i);
+    float2 sr[4], si[4];                    // four independent chains (rows mod 4) hide the add latency
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sr[u] = si[u] = make_float2(0.f, 0.f);
+    auto mac = [&](float2& ar, float2& ai, float4 v, float4 w) {
       const float2 vr = make_float2(v.x, v.y), vi = make_float2(v.z, v.w);
       const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
       // conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr)
-      df_mac(sr, vr, wr);
-      df_mac(sr, vi, wi);
-      df_mac(si, vr, wi);
-      df_mac(si, df_neg(vi), wr);
+      df_mac(ar, vr, wr);
+      df_mac(ar, vi, wi);
+      df_mac(ai, vr, wi);
+      df_mac(ai, df_neg(vi), wr);
     };
     int r = 0;
     for (; r + 4 <= nrows; r += 4) {
@@ -336,10 +364,15 @@ __device__ void project_partial(const HayArgs& A, const float4* wsm, int row0, i
 #pragma unroll
       for (int u = 0; u < 4; ++u) v[u] = Vi[r + u];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) mac(v[u], wsm[r + u]);
+      for (int u = 0; u < 4; ++u) mac(sr[u], si[u], v[u], wsm[r + u]);
     }
-    for (; r < nrows; ++r) mac(Vi[r], wsm[r]);
-    A.hpart[(size_t)A.grank * A.nsteps + i] = cdf_val(make_float4(sr.x, sr.y, si.x, si.y));
+    for (; r < nrows; ++r) mac(sr[0], si[0], Vi[r], wsm[r]);
+#pragma unroll
+    for (int u = 1; u < 4; ++u) {
+      df_add(sr[0], sr[u]);
+      df_add(si[0], si[u]);
+    }
+    A.hpart[(size_t)A.grank * A.nsteps + i] = cdf_val(make_float4(sr[0].x, sr[0].y, si[0].x, si[0].y));
   }
 }
 
@@ -361,9 +394,8 @@ __device__ void reduce_coeffs(const HayArgs& A, double2* h, int n) {
 // w[r] -= sum_i V[i][r] h[i] over own rows.  Threads are (vector group, row) with rows fastest:
 // each sums every ng-th basis vector for its row with independent, unrolled loads, then the
 // ng partials of a row are added in a fixed order.  h is staged split (hi, lo) in hs.
-__device__ void subtract_projection(const HayArgs& A, float4* wsm, float4* red, float4* hs, const double2* h,
-                                    int row0, int nrows, int n) {
-  const int dim = A.dim;
+__device__ void subtract_projection(const BasisRows& Vb, float4* wsm, float4* red, float4* hs, const double2* h,
+                                    int nrows, int n) {
   for (int i = threadIdx.x; i < n; i += kThreads) hs[i] = cdf_split(__ldcg(h + i));
   __syncthreads();
   for (int rb = 0; rb < nrows; rb += kThreads) {
@@ -371,27 +403,34 @@ __device__ void subtract_projection(const HayArgs& A, float4* wsm, float4* red, 
     const int ng = kThreads / nr;
     const int r = threadIdx.x % nr, ig = threadIdx.x / nr;
     if (ig < ng) {
-      float2 sr = make_float2(0.f, 0.f), si = make_float2(0.f, 0.f);
-      auto mac = [&](float4 v, float4 c) {
+      float2 sr[4], si[4];                  // four independent chains
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sr[u] = si[u] = make_float2(0.f, 0.f);
+      auto mac = [&](float2& ar, float2& ai, float4 v, float4 c) {
         const float2 vr = make_float2(v.x, v.y), vi = make_float2(v.z, v.w);
         const float2 cr = make_float2(c.x, c.y), ci = make_float2(c.z, c.w);
         // v c = (vr cr - vi ci) + i (vr ci + vi cr)
-        df_mac(sr, vr, cr);
-        df_mac(sr, df_neg(vi), ci);
-        df_mac(si, vr, ci);
-        df_mac(si, vi, cr);
+        df_mac(ar, vr, cr);
+        df_mac(ar, df_neg(vi), ci);
+        df_mac(ai, vr, ci);
+        df_mac(ai, vi, cr);
       };
-      const float4* Vr = A.V + row0 + rb + r;
+      const int rr = rb + r;
       int i = ig;
       for (; i + 3 * ng < n; i += 4 * ng) {
         float4 v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = Vr[(size_t)(i + u * ng) * dim];
+        for (int u = 0; u < 4; ++u) v[u] = Vb.row(i + u * ng)[rr];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) mac(v[u], hs[i + u * ng]);
+        for (int u = 0; u < 4; ++u) mac(sr[u], si[u], v[u], hs[i + u * ng]);
       }
-      for (; i < n; i += ng) mac(Vr[(size_t)i * dim], hs[i]);
-      red[ig * nr + r] = make_float4(sr.x, sr.y, si.x, si.y);
+      for (; i < n; i += ng) mac(sr[0], si[0], Vb.row(i)[rr], hs[i]);
+#pragma unroll
+      for (int u = 1; u < 4; ++u) {
+        df_add(sr[0], sr[u]);
+        df_add(si[0], si[u]);
+      }
+      red[ig * nr + r] = make_float4(sr[0].x, sr[0].y, si[0].x, si[0].y);
     }
     __syncthreads();
     if (threadIdx.x < nr) {
@@ -437,6 +476,24 @@ __device__ double all_cta_sum(const HayArgs& A, int which, double* red1) {
   return bc;
 }
 
+// both sums of npart[c][0] and npart[c][1] in one pass by warp 0 (identical order in every CTA)
+__device__ double2 all_cta_sum2(const HayArgs& A, double2* red2) {
+  if (threadIdx.x < 32) {
+    double2 v = make_double2(0.0, 0.0);
+    for (int c = threadIdx.x; c < A.gsize; c += 32) {
+      const double2 p = __ldcg(reinterpret_cast<const double2*>(A.npart) + c);
+      v.x += p.x;
+      v.y += p.y;
+    }
+    v = warp_sum(v);
+    if (threadIdx.x == 0) red2[0] = v;
+  }
+  __syncthreads();
+  const double2 t = red2[0];
+  __syncthreads();
+  return t;
+}
+
 constexpr int kMaxBatch = 24;
 
 // One system of a batched launch (pointers into that system's workspace).
@@ -459,12 +516,17 @@ struct HaySys {
 
 struct HayBatch {
   int nsys, nsteps, nw, rows_max;   // rows_max: largest rows-per-CTA over the systems
+  int xtile;                        // columns of v_j staged per pass
+  int vsk;                          // basis vectors whose own rows are kept in shared memory
   double eta;
   const double* omega;
   int* status;
   HaySys s[kMaxBatch];
 };
 
+// The CTA's rows of the first B.vsk basis vectors also live in shared memory (they are read only by
+// this CTA), so most projections and updates read shared memory; the global copy serves the rest
+// and the adjoint.
 __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(const __grid_constant__ HayBatch B) {
   int g = 0;
   while (g + 1 < B.nsys && (int)blockIdx.x >= B.s[g + 1].cta0) ++g;
@@ -497,6 +559,11 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(const __grid_const
   float4* wsm = dyn;                                // own rows of w (double-float)
   float4* hs = dyn + B.rows_max;                    // projection coefficients (double-float)
   float2* xs = reinterpret_cast<float2*>(hs + B.nsteps);   // column tile of v_j (FP32)
+  float4* vsm = reinterpret_cast<float4*>(xs + B.xtile);   // [vsk][rows_max] own rows of the first basis vectors
+  if (B.vsk > 0 && (reinterpret_cast<uintptr_t>(vsm) & 15) != 0) {   // float4 rows must be 16-byte aligned
+    if (threadIdx.x == 0) atomicCAS(B.status, 0, (int)BSE_ERR_CUDA);
+    return;
+  }
   __shared__ float4 red[kThreads];
   __shared__ double red1[kWarps];
   const int dim = A.dim;
@@ -520,8 +587,10 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(const __grid_const
     const double2 p = A.P[row0 + r];
     const double2 v = make_double2(p.x * pinv, p.y * pinv);
     A.V[row0 + r] = cdf_split(v);
+    if (B.vsk > 0) vsm[r] = cdf_split(v);
     A.vf[row0 + r] = make_float2((float)v.x, (float)v.y);
   }
+  const BasisRows Vb{vsm, A.V + row0, B.vsk, B.rows_max, dim};
   if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
 
   int done = A.nsteps;
@@ -529,8 +598,8 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(const __grid_const
   for (int j = 0; j < A.nsteps; ++j) {
     // w = H v_j on own rows: v_j staged in shared memory in column tiles, H streamed once
     for (int r = threadIdx.x; r < nrows; r += kThreads) wsm[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int col0 = 0; col0 < dim; col0 += kXTile) {
-      const int cols = min(kXTile, dim - col0);
+    for (int col0 = 0; col0 < dim; col0 += B.xtile) {
+      const int cols = min(B.xtile, dim - col0);
       __syncthreads();
       for (int c = threadIdx.x; c < cols; c += kThreads) {
         const float2 x = __ldcg(A.vf + col0 + c);
@@ -553,35 +622,43 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(const __grid_const
       }
     }
     __syncthreads();
-    double hv2 = 0.0;
-    for (int r = threadIdx.x; r < nrows; r += kThreads) {
-      const double2 s = cdf_val(wsm[r]);
-      hv2 += s.x * s.x + s.y * s.y;
+    if (warp == 0) {                        // |H v_j|^2 only sets the breakdown threshold: FP32, one warp
+      float hv2 = 0.f;
+      for (int r = lane; r < nrows; r += 32) {
+        const float4 w = wsm[r];
+        hv2 += w.x * w.x + w.z * w.z;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) hv2 += __shfl_xor_sync(0xffffffffu, hv2, o);
+      if (lane == 0) A.npart[2 * A.grank + 1] = hv2;
     }
-    hv2 = block_sum(hv2, red1);
-    if (threadIdx.x == 0) A.npart[2 * A.grank + 1] = hv2;
-    __syncthreads();
-    project_partial(A, wsm, row0, nrows, j + 1);
+    project_partial(A, Vb, wsm, nrows, j + 1);
     if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
     reduce_coeffs(A, A.h1, j + 1);
     if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
-    subtract_projection(A, wsm, red, hs, A.h1, row0, nrows, j + 1);
-    project_partial(A, wsm, row0, nrows, j + 1);
+    subtract_projection(Vb, wsm, red, hs, A.h1, nrows, j + 1);
+    project_partial(A, Vb, wsm, nrows, j + 1);
     if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
     reduce_coeffs(A, A.h2, j + 1);
     if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
-    subtract_projection(A, wsm, red, hs, A.h2, row0, nrows, j + 1);
-    double ww = 0.0;
-    for (int r = threadIdx.x; r < nrows; r += kThreads) {
-      const double2 w = cdf_val(wsm[r]);
-      ww += w.x * w.x + w.y * w.y;
-      A.vf[row0 + r] = make_float2((float)w.x, (float)w.y);   // published unnormalised
+    subtract_projection(Vb, wsm, red, hs, A.h2, nrows, j + 1);
+    for (int r = threadIdx.x; r < nrows; r += kThreads) {     // published unnormalised
+      const float4 w = wsm[r];
+      A.vf[row0 + r] = make_float2(w.x + w.y, w.z + w.w);
     }
-    ww = block_sum(ww, red1);
-    if (threadIdx.x == 0) A.npart[2 * A.grank] = ww;
+    if (warp == 0) {                        // |w|^2 of own rows in FP64 by one warp (FP64 issues slowly)
+      double ww = 0.0;
+      for (int r = lane; r < nrows; r += 32) {
+        const double2 w = cdf_val(wsm[r]);
+        ww += w.x * w.x + w.y * w.y;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ww += __shfl_xor_sync(0xffffffffu, ww, o);
+      if (lane == 0) A.npart[2 * A.grank] = ww;
+    }
     if (!grid_barrier(A.bar, A.status, (unsigned)A.gsize)) return;
-    const double bn2 = all_cta_sum(A, 0, red1);
-    const double sc2 = all_cta_sum(A, 1, red1);
+    const double2 sums = all_cta_sum2(A, reinterpret_cast<double2*>(red));
+    const double bn2 = sums.x, sc2 = sums.y;
     const double2 c1 = __ldcg(A.h1 + j), c2 = __ldcg(A.h2 + j);
     const double aj = c1.x + c2.x;
     const double bn = sqrt(bn2);
@@ -601,7 +678,9 @@ __global__ __launch_bounds__(kThreads, 1) void haydock_kernel(const __grid_const
     float4* Vn = A.V + (size_t)(j + 1) * dim + row0;   // own rows only: no grid barrier needed
     for (int r = threadIdx.x; r < nrows; r += kThreads) {
       const double2 w = cdf_val(wsm[r]);
-      Vn[r] = cdf_split(make_double2(w.x * binv, w.y * binv));
+      const float4 v = cdf_split(make_double2(w.x * binv, w.y * binv));
+      Vn[r] = v;
+      if (j + 1 < B.vsk) vsm[(size_t)(j + 1) * B.rows_max + r] = v;
     }
     vscale = (float)binv;
   }
@@ -722,8 +801,16 @@ int run_haydock_batch(const HayJob* jobs, int n, int nsteps, const double* omega
     const int e = (int)cudaMemsetAsync(S.bar, 0, 2 * sizeof(unsigned), st);
     if (e) return e;
   }
-  const size_t dyn = ((size_t)B.rows_max + (size_t)nsteps) * sizeof(float4) + (size_t)kXTile * sizeof(float2);
-  if (dyn > 200 * 1024) return -1;
+  // x tile of up to 8192 columns, then as many basis vectors' own rows in shared memory as fit
+  int dim_max = 0;
+  for (int i = 0; i < n; ++i) dim_max = jobs[i].d->dim > dim_max ? jobs[i].d->dim : dim_max;
+  B.xtile = dim_max < kXTile ? (dim_max + 1) / 2 * 2 : kXTile;   // even: the basis rows after it stay 16-byte aligned
+  const size_t fixed = ((size_t)B.rows_max + (size_t)nsteps) * sizeof(float4) + (size_t)B.xtile * sizeof(float2);
+  if (fixed > kDynMax || fixed % sizeof(float4) != 0) return -1;
+  const size_t per_vec = (size_t)B.rows_max * sizeof(float4);
+  const size_t fit = (kDynMax - fixed) / per_vec;
+  B.vsk = (int)(fit < (size_t)nsteps ? fit : (size_t)nsteps);
+  const size_t dyn = fixed + (size_t)B.vsk * per_vec;
   cudaFuncSetAttribute((const void*)haydock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, haydock_kernel, kThreads, dyn);
   if (occ < 1) return -1;
