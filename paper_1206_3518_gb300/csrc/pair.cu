@@ -114,19 +114,24 @@ __global__ __launch_bounds__(kThreads) void realspace_kernel(DevSys d, const flo
 // Template parameters: grid N1 x N2 x N3; kept windows |f2| <= F2, |f3| <= F3; PMAX band
 // products and BMAX band slabs per CTA; ROWS z-lines per pipelined chunk; PPT sphere points
 // per thread in stage 3; THREADS per CTA; MERGED = one CTA computes both the vv' and the cc'
-// products of a block (else one CTA per block and group).
-template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int PPT, int THREADS, bool MERGED>
+// products of a block (else one CTA per block and group); SINGLE = whole x-slabs (ROWS = N2) in
+// one buffer whose refill is issued after stage 1 and lands during stages 2 and 3 (else two
+// buffers of ROWS-line chunks, the next chunk loading while the current one is transformed).
+template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int PPT, int THREADS, bool MERGED,
+          bool SINGLE>
 struct PairCfg {
   static constexpr int M2 = 2 * F2 + 1, M3 = 2 * F3 + 1;
   static constexpr int LD = N3 + 2;    // z-line stride in shared memory: 16-B aligned rows, float4 reads conflict-free
   static constexpr int NCH = N1 * (N2 / ROWS);
   static_assert(N2 % ROWS == 0, "ROWS must divide N2");
   static_assert(BMAX <= THREADS, "one band copy per thread and chunk");
+  static_assert(!SINGLE || ROWS == N2, "a single buffer holds whole slabs");
+  static constexpr int NBUF = SINGLE ? 1 : 2;
   static_assert(((N3 + 2) * 8) % 16 == 0, "copy box rows are 16-byte multiples");
   static constexpr int S1P = (N2 + 1) * M3;   // product stride of S1 (one padding row: spreads banks)
   static constexpr int BSTR = (ROWS * LD * 8 + 127) / 128 * 16;   // band stride in float2: 128-byte multiple
   static size_t smem(int ng_max) {
-    return 24 + sizeof(float2) * ((size_t)2 * BMAX * BSTR + (size_t)PMAX * S1P + (size_t)PMAX * M2 * M3 + N1) +
+    return 24 + sizeof(float2) * ((size_t)NBUF * BMAX * BSTR + (size_t)PMAX * S1P + (size_t)PMAX * M2 * M3 + N1) +
            sizeof(int2) * (size_t)ng_max;
   }
 };
@@ -259,17 +264,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
-template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int PPT, int THREADS, bool MERGED>
+template <int N1, int N2, int N3, int F2, int F3, int PMAX, int BMAX, int ROWS, int PPT, int THREADS, bool MERGED,
+          bool SINGLE>
 __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2* __restrict__ u,
                                                           float2* __restrict__ out, int mode, int q0, int nqc,
                                                           long long vbase, int* status,
                                                           const __grid_constant__ CUtensorMap tm) {
-  using C = PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, PPT, THREADS, MERGED>;
+  using C = PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, PPT, THREADS, MERGED, SINGLE>;
   constexpr int M2 = C::M2, M3 = C::M3, LD = C::LD, NCH = C::NCH, S1P = C::S1P, BSTR = C::BSTR;
   constexpr int CPR = N2 / ROWS;            // chunks per slab
   extern __shared__ __align__(128) float4 sm4[];
-  float2* ub = reinterpret_cast<float2*>(sm4);          // [2][BMAX][BSTR]: ROWS rows of LD per band
-  float2* S1 = ub + 2 * BMAX * BSTR;                    // [PMAX][N2 (+1 pad)][M3]
+  float2* ub = reinterpret_cast<float2*>(sm4);          // [NBUF][BMAX][BSTR]: ROWS rows of LD per band
+  float2* S1 = ub + C::NBUF * BMAX * BSTR;              // [PMAX][N2 (+1 pad)][M3]
   float2* S2 = S1 + PMAX * S1P;                         // [PMAX][M2][M3]
   float2* tw1 = S2 + PMAX * M2 * M3;                    // [N1] exp(-2 pi i g j1/N1) of the current slab
   uint64_t* bars = reinterpret_cast<uint64_t*>(tw1 + N1);   // [2] chunk landed (one per buffer)
@@ -316,16 +322,19 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
   __syncthreads();                          // barriers initialised, sphere table filled
 
   bool alive = true;                        // false once one of this thread's waits gave up
+  // chunk c lands in buffer bufi(c), counted on mbarrier bufi(c) in phase phase(c)
+  auto bufi = [](int c) { return SINGLE ? 0 : (c & 1); };
+  auto phase = [](int c) { return (uint32_t)(SINGLE ? c : (c >> 1)) & 1u; };
   auto issue = [&](int c) {
     if (!alive) return;
     const int j1 = c / CPR, r0 = (c - j1 * CPR) * ROWS;
-    const uint32_t bar = bar0 + 8u * (uint32_t)(c & 1);
+    const uint32_t bar = bar0 + 8u * (uint32_t)bufi(c);
     if (tid == 0) mbar_expect_tx(bar, chunk_bytes);
     if (tid < nbands) {
       const int y = (int)(lbase + j1 * N2 + r0);
       asm volatile(
           "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-          ::"r"(ldst + (uint32_t)(c & 1) * kBuf), "l"(reinterpret_cast<uint64_t>(&tm)), "r"(0), "r"(y), "r"(bar)
+          ::"r"(ldst + (uint32_t)bufi(c) * kBuf), "l"(reinterpret_cast<uint64_t>(&tm)), "r"(0), "r"(y), "r"(bar)
           : "memory");
     }
   };
@@ -343,16 +352,17 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
 
   // Barriers: a chunk that does not end a slab ends with one (its buffer is refilled next);
   // a slab-end chunk has one before stage 2 and one before stage 3, which also order every
-  // thread's wait on a buffer's mbarrier before the next expect_tx on it.
+  // thread's wait on a buffer's mbarrier before the next expect_tx on it.  With a single
+  // buffer the next slab is issued after the barrier that ends stage 1.
   issue(0);
   for (int c = 0; c < NCH; ++c) {
-    if (c + 1 < NCH) issue(c + 1);
-    if (alive && !mbar_wait(bar0 + 8u * (uint32_t)(c & 1), (uint32_t)(c >> 1) & 1u)) {
+    if (!SINGLE && c + 1 < NCH) issue(c + 1);
+    if (alive && !mbar_wait(bar0 + 8u * (uint32_t)bufi(c), phase(c))) {
       alive = false;                        // a copy never landed: stop waiting and issuing, report below
       s_fail = 1;
     }
     const int j1 = c / CPR, r0 = (c - j1 * CPR) * ROWS;
-    const float2* buf = ub + (size_t)(c & 1) * BMAX * BSTR;
+    const float2* buf = ub + (size_t)bufi(c) * BMAX * BSTR;
 #pragma unroll
     for (int k1 = 0; k1 < K1; ++k1) {                           // stage 1: product + z FFT
       if (it1[k1] >= P * ROWS) continue;
@@ -374,6 +384,7 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
     }
     if (r0 + ROWS == N2) {                                       // slab complete
       __syncthreads();
+      if (SINGLE && c + 1 < NCH) issue(c + 1);                  // lands during stages 2 and 3
       for (int it = tid; it < P * M3; it += THREADS) {          // stage 2: y FFT of kept planes
         const int p = it / M3, m3 = it - p * M3;
         float2 y[N2];
@@ -404,8 +415,8 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
   __syncthreads();
   if (s_fail) {                             // bounded wait for copies still in flight, then report
     if (tid == 0) {
-      if (NCH >= 2) mbar_wait(bar0 + 8u * (uint32_t)((NCH - 2) & 1), (uint32_t)((NCH - 2) >> 1) & 1u);
-      mbar_wait(bar0 + 8u * (uint32_t)((NCH - 1) & 1), (uint32_t)((NCH - 1) >> 1) & 1u);
+      if (!SINGLE && NCH >= 2) mbar_wait(bar0 + 8u * (uint32_t)bufi(NCH - 2), phase(NCH - 2));
+      mbar_wait(bar0 + 8u * (uint32_t)bufi(NCH - 1), phase(NCH - 1));
       atomicCAS(status, 0, (int)BSE_ERR_TIMEOUT);
     }
     return;
@@ -467,26 +478,27 @@ struct Variant {
   size_t (*pair_smem)(int);
 };
 
-#define BSE_VARIANT(N1, N2, N3, F1, F2, F3, PMAX, BMAX, ROWS, PPT, THREADS, MERGED)                              \
+#define BSE_VARIANT(N1, N2, N3, F1, F2, F3, PMAX, BMAX, ROWS, PPT, THREADS, MERGED, SINGLE)                      \
   Variant {                                                                                                      \
     N1, N2, N3, F1, F2, F3, PMAX, BMAX, THREADS, PPT, ROWS, MERGED, realspace_kernel<N1, N2, N3, F1, F2, F3>,    \
         RsCfg<N1, N2, N3, F1, F2, F3>::smem,                                                                     \
-        pair_kernel<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, PPT, THREADS, MERGED>,                                 \
-        PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, PPT, THREADS, MERGED>::smem                                \
+        pair_kernel<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, PPT, THREADS, MERGED, SINGLE>,                         \
+        PairCfg<N1, N2, N3, F2, F3, PMAX, BMAX, ROWS, PPT, THREADS, MERGED, SINGLE>::smem                        \
   }
 
 // Candidate tile shapes per grid; the planner takes the first valid one unless a variant was chosen
 // (by the autotuner or the caller).  The hexagonal-sheet grid has variants sized for 2-5, 8-10 and
-// 18 band products, the fcc 8x8x8 grid two chunk heights.
+// 18 band products, the fcc 8x8x8 grid three chunk heights (whole slabs measured fastest).
 const Variant kVariants[] = {
-    BSE_VARIANT(8, 8, 8, 2, 2, 2, 18, 12, 8, 1, 128, true),          // small test cells
-    BSE_VARIANT(24, 24, 24, 3, 3, 3, 18, 12, 24, 1, 448, true),      // fcc 4x4x4, 3v3c
-    BSE_VARIANT(32, 32, 32, 5, 5, 5, 25, 14, 16, 1, 416, true),      // fcc 8x8x8, 3v4c
-    BSE_VARIANT(32, 32, 32, 5, 5, 5, 25, 14, 8, 2, 224, true),       //   half-height chunks
-    BSE_VARIANT(48, 48, 48, 6, 6, 6, 16, 8, 16, 3, 256, false),      // fcc 12x12x12, 4v4c
-    BSE_VARIANT(12, 12, 48, 2, 2, 10, 18, 12, 12, 1, 224, true),     // hexagonal sheets, <= 3v3c
-    BSE_VARIANT(12, 12, 48, 2, 2, 10, 10, 8, 12, 1, 128, true),      //   <= 10 products, <= 4 bands
-    BSE_VARIANT(12, 12, 48, 2, 2, 10, 5, 6, 12, 2, 64, true),        //   1v2c, 2v1c, 1v1c
+    BSE_VARIANT(8, 8, 8, 2, 2, 2, 18, 12, 8, 1, 128, true, false),         // small test cells
+    BSE_VARIANT(24, 24, 24, 3, 3, 3, 18, 12, 24, 1, 448, true, false),     // fcc 4x4x4, 3v3c
+    BSE_VARIANT(32, 32, 32, 5, 5, 5, 25, 14, 32, 1, 416, true, true),      // fcc 8x8x8, 3v4c: whole slabs
+    BSE_VARIANT(32, 32, 32, 5, 5, 5, 25, 14, 16, 1, 416, true, false),     //   half slabs, two buffers
+    BSE_VARIANT(32, 32, 32, 5, 5, 5, 25, 14, 8, 2, 224, true, false),      //   half-height chunks
+    BSE_VARIANT(48, 48, 48, 6, 6, 6, 16, 8, 16, 3, 256, false, false),     // fcc 12x12x12, 4v4c
+    BSE_VARIANT(12, 12, 48, 2, 2, 10, 18, 12, 12, 1, 224, true, false),    // hexagonal sheets, <= 3v3c
+    BSE_VARIANT(12, 12, 48, 2, 2, 10, 10, 8, 12, 1, 128, true, false),     //   <= 10 products, <= 4 bands
+    BSE_VARIANT(12, 12, 48, 2, 2, 10, 5, 6, 12, 2, 64, true, false),       //   1v2c, 2v1c, 1v1c
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
