@@ -305,6 +305,16 @@ bse_status bse_set_pair_variant(bse_plan* plan, int s, int index);
 bse_status bse_autotune_pair(bse_plan* plan, int s, void* ws, size_t ws_bytes, void* rho_dir, int q_begin,
                              int q_end, int reps, float* ms, int cap, int* chosen, void* stream);
 
+/*
+ * Failure injection: limit (ns) of every grid-barrier wait of the spectrum kernels (steps A7,
+ * A8 and their recomputation in the adjoint) on the current device; default 2e9.  A wait that
+ * exceeds it sets BSE_ERR_TIMEOUT in the plan's status word and the kernel returns; with 0
+ * every wait gives up at once, which exercises that path without a fault or a hang.  The
+ * other kernels' waits keep their fixed 2 s limit.  Synchronous; not capturable.  No
+ * counterpart in the paper.  Errors: BSE_ERR_CUDA.
+ */
+bse_status bse_set_wait_limit(unsigned long long ns);
+
 /* Synchronise the stream and return (then clear) the plan's device status word. */
 bse_status bse_status_read(bse_plan* plan, void* stream);
 

@@ -27,7 +27,7 @@ EXPORTED = [
     "bse_last_error", "bse_plan_create", "bse_plan_create_host", "bse_plan_destroy", "bse_plan_info", "bse_gvectors",
     "bse_pair_blocks", "bse_workspace_size", "bse_rho_dir_count", "bse_pair_densities",
     "bse_build_kernel", "bse_apply_H", "bse_spectrum", "bse_spectrum_static", "bse_spectrum_batch", "bse_spectrum_backward", "bse_status_read",
-    "bse_pair_variants", "bse_set_pair_variant", "bse_autotune_pair",
+    "bse_pair_variants", "bse_set_pair_variant", "bse_autotune_pair", "bse_set_wait_limit",
 ]
 
 
@@ -91,6 +91,7 @@ def load():
     lib.bse_status_read.argtypes = [vp, vp]
     lib.bse_pair_variants.argtypes = [vp, i, ctypes.POINTER(BsePairVariant), i, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.bse_set_pair_variant.argtypes = [vp, i, i]
+    lib.bse_set_wait_limit.argtypes = [ctypes.c_ulonglong]
     lib.bse_autotune_pair.argtypes = [vp, i, vp, sz, vp, i, i, i, ctypes.POINTER(ctypes.c_float), i,
                                       ctypes.POINTER(i), vp]
     for name in EXPORTED:
@@ -285,3 +286,8 @@ def bse_autotune_pair(plan, s, ws, rho_dir, q_begin, q_end, reps=3):
                                     ms, 64, ctypes.byref(chosen), _stream()))
     n = len(bse_pair_variants(plan, s)[0])
     return [float(ms[k]) for k in range(n)], chosen.value
+
+
+def bse_set_wait_limit(ns):
+    """Limit of each grid-barrier wait of the spectrum kernels on the current device (failure injection)."""
+    _check(load().bse_set_wait_limit(int(ns)))

@@ -54,6 +54,9 @@ __device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Limit of one grid-barrier wait (ns); settable per device for failure-injection tests.
+__device__ unsigned long long g_wait_limit_ns = 2000000000ull;
+
 // Barrier over the gsize CTAs of one system's group, on a (count, generation) pair: arrivals are
 // acquire-release atomics, the last arrival resets the count and releases the generation, the
 // others poll it with acquire loads.  False if the wait timed out or another CTA already
@@ -79,7 +82,7 @@ __device__ bool grid_barrier(unsigned* bar, int* status, unsigned gsize) {
             good = 0;
             break;
           }
-          if (globaltimer() - t0 > 2000000000ull) {
+          if (globaltimer() - t0 > g_wait_limit_ns) {
             atomicCAS(status, 0, (int)BSE_ERR_TIMEOUT);
             good = 0;
             break;
@@ -817,6 +820,8 @@ int run_haydock_batch(const HayJob* jobs, int n, int nsteps, const double* omega
   void* args[] = {&B};
   return (int)cudaLaunchCooperativeKernel((const void*)haydock_kernel, dim3(grid), dim3(kThreads), args, dyn, st);
 }
+
+int set_wait_limit(unsigned long long ns) { return (int)cudaMemcpyToSymbol(g_wait_limit_ns, &ns, sizeof(ns)); }
 
 // Shared with the adjoint: one system into a caller-laid-out workspace.
 int run_haydock(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw, double eta,

@@ -79,6 +79,7 @@ int launch_gemm_wr(const DevSys& d, const void* rho_dir, int q_begin, int q_end,
                    const void* W, void* X, int side_c, void* stream);
 
 size_t spectrum_static_capacity();
+int set_wait_limit(unsigned long long ns);
 int launch_spectrum_static(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw,
                            double eta, double* eps2, double* ab, int* steps_done, int* status, void* stream);
 int launch_apply_h(const DevSys& d, const void* H, const void* X, void* Y, int nvec, void* stream);

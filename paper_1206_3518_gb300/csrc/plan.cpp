@@ -676,6 +676,10 @@ bse_status bse_spectrum_backward(bse_plan* plan, int s, const void* H, const voi
   return cuda_check(e, "spectrum backward");
 }
 
+bse_status bse_set_wait_limit(unsigned long long ns) {
+  return cuda_check(set_wait_limit(ns), "set wait limit");
+}
+
 bse_status bse_status_read(bse_plan* plan, void* stream) {
   if (!plan || !plan->d_status) return set_error(BSE_ERR_ARG, "plan is NULL or host-only");
   bse_status st = cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
