@@ -61,13 +61,15 @@ typedef enum {
   BSE_WS_PAIR = 0,      /* bse_pair_densities: real-space wavefunctions u_nk(r) */
   BSE_WS_KERNEL = 1,    /* bse_build_kernel: W.rho products of one q chunk */
   BSE_WS_SPECTRUM = 2,  /* bse_spectrum: Krylov basis, vectors, partial sums */
-  BSE_WS_BACKWARD = 3   /* bse_spectrum_backward: basis, dL/dH, chain products */
+  BSE_WS_BACKWARD = 3,  /* bse_spectrum_backward: basis, dL/dH, chain products */
+  BSE_WS_SCREEN = 4     /* bse_screening: dielectric matrices of one q chunk (arg = chunk) */
 } bse_ws_kind;
 
 /* Stage flags for bse_pair_densities and bse_build_kernel. */
 #define BSE_PD_REALSPACE 1u   /* A1: fill u_nk(r) in the workspace            */
 #define BSE_PD_EXCHANGE  2u   /* A2 exchange set rho_x and the A6 dipole P     */
 #define BSE_PD_DIRECT    4u   /* A2 direct set rho_vv', rho_cc' of a q range   */
+#define BSE_PD_CHI0      8u   /* rho_vc^{k,k+q} for all k, q of a range (screening input) */
 #define BSE_BK_INIT      1u   /* A3 + A5 diagonal: H = diag + 2 K^x (upper)    */
 #define BSE_BK_DIRECT    2u   /* A4 + A5: H -= K^d for a q range, mirror       */
 
@@ -304,6 +306,29 @@ bse_status bse_pair_variants(const bse_plan* plan, int s, bse_pair_variant* out,
 bse_status bse_set_pair_variant(bse_plan* plan, int s, int index);
 bse_status bse_autotune_pair(bse_plan* plan, int s, void* ws, size_t ws_bytes, void* rho_dir, int q_begin,
                              int q_end, int reps, float* ms, int cap, int* chosen, void* stream);
+
+/*
+ * Static RPA screening from the system's own states (Sec. II A-B, Eqs. chi0_GG and
+ * epsilon_-1; the W_GG'(q) form of Sec. III A).  Produces the W that bse_build_kernel takes,
+ * for q in [q_begin, q_end):
+ *   chi0_GG'(q) = 4/(Omega Nk) sum_{k,v,c} rho(G) conj(rho(G')) / (e_vk - e_c,k+q),
+ *   rho = rho_vc^{k,k+q}(G) (bse_pair_densities with BSE_PD_CHI0), bare energies with the
+ *   system's gap floor; eps = 1 - v^1/2 chi0 v^1/2 (v^1/2 = sqrt(4 pi)/|q+G|); at q = 0 the
+ *   G = 0 row and column from the k.p dipole P (bse_pair_densities, BSE_PD_EXCHANGE);
+ *   eps^-1 by `iterations` Newton-Schulz steps from 2/(1 + R) I (R: Gershgorin bound);
+ *   W = v^1/2 eps^-1 v^1/2, at q = 0 head [eps^-1]_00 12 pi/q_c^2 (q_c^3 = 6 pi^2/(Omega Nk))
+ *   and zero wings.
+ * rho_chi  complex64 [(q_end - q_begin) Nk Nv Nc][ng_max] from BSE_PD_CHI0 for the same range;
+ *          overwritten with the scaled pair vectors.
+ * energies float64 [Nk][Nb];  P complex128 [dim] (needed when q_begin = 0).
+ * W        complex64 [Nq][ng_max][ng_max]; the rows of q in the range are written (zero padded).
+ * residual float32 [q_end - q_begin] on the device (optional): max |I - eps X| per q.
+ * ws       bse_workspace_size(BSE_WS_SCREEN, q_end - q_begin) bytes.
+ * Errors: BSE_ERR_ARG, BSE_ERR_WORKSPACE, BSE_ERR_UNSUPPORTED (slab Coulomb).
+ */
+bse_status bse_screening(bse_plan* plan, int s, void* rho_chi, const double* energies, const void* P, int q_begin,
+                         int q_end, int iterations, void* W, float* residual, void* ws, size_t ws_bytes,
+                         void* stream);
 
 /*
  * Failure injection: limit (ns) of every grid-barrier wait of the spectrum kernels (steps A7,

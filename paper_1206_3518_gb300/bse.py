@@ -19,15 +19,15 @@ BSE_OK, BSE_ERR_ARG, BSE_ERR_CUDA, BSE_ERR_NONFINITE, BSE_ERR_TIMEOUT, BSE_ERR_U
 BSE_LATTICE_FCC, BSE_LATTICE_HEX = 0, 1
 BSE_COULOMB_3D, BSE_COULOMB_SLAB = 0, 1
 BSE_PREC_FP32, BSE_PREC_BF16X3 = 0, 1
-BSE_WS_PAIR, BSE_WS_KERNEL, BSE_WS_SPECTRUM, BSE_WS_BACKWARD = 0, 1, 2, 3
-BSE_PD_REALSPACE, BSE_PD_EXCHANGE, BSE_PD_DIRECT = 1, 2, 4
+BSE_WS_PAIR, BSE_WS_KERNEL, BSE_WS_SPECTRUM, BSE_WS_BACKWARD, BSE_WS_SCREEN = 0, 1, 2, 3, 4
+BSE_PD_REALSPACE, BSE_PD_EXCHANGE, BSE_PD_DIRECT, BSE_PD_CHI0 = 1, 2, 4, 8
 BSE_BK_INIT, BSE_BK_DIRECT = 1, 2
 
 EXPORTED = [
     "bse_last_error", "bse_plan_create", "bse_plan_create_host", "bse_plan_destroy", "bse_plan_info", "bse_gvectors",
     "bse_pair_blocks", "bse_workspace_size", "bse_rho_dir_count", "bse_pair_densities",
     "bse_build_kernel", "bse_apply_H", "bse_spectrum", "bse_spectrum_static", "bse_spectrum_batch", "bse_spectrum_backward", "bse_status_read",
-    "bse_pair_variants", "bse_set_pair_variant", "bse_autotune_pair", "bse_set_wait_limit",
+    "bse_pair_variants", "bse_set_pair_variant", "bse_autotune_pair", "bse_set_wait_limit", "bse_screening",
 ]
 
 
@@ -92,6 +92,7 @@ def load():
     lib.bse_pair_variants.argtypes = [vp, i, ctypes.POINTER(BsePairVariant), i, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.bse_set_pair_variant.argtypes = [vp, i, i]
     lib.bse_set_wait_limit.argtypes = [ctypes.c_ulonglong]
+    lib.bse_screening.argtypes = [vp, i, vp, vp, vp, i, i, i, vp, vp, vp, sz, vp]
     lib.bse_autotune_pair.argtypes = [vp, i, vp, sz, vp, i, i, i, ctypes.POINTER(ctypes.c_float), i,
                                       ctypes.POINTER(i), vp]
     for name in EXPORTED:
@@ -291,3 +292,9 @@ def bse_autotune_pair(plan, s, ws, rho_dir, q_begin, q_end, reps=3):
 def bse_set_wait_limit(ns):
     """Limit of each grid-barrier wait of the spectrum kernels on the current device (failure injection)."""
     _check(load().bse_set_wait_limit(int(ns)))
+
+
+def bse_screening(plan, s, rho_chi, energies, P, q_begin, q_end, iterations, W, residual, ws):
+    """Static RPA W of q in [q_begin, q_end) from BSE_PD_CHI0 pair densities (rho_chi is overwritten)."""
+    _check(load().bse_screening(plan.handle, s, _ptr(rho_chi), _ptr(energies), _ptr(P), q_begin, q_end,
+                                int(iterations), _ptr(W), _ptr(residual), _ptr(ws), _nbytes(ws), _stream()))

@@ -29,6 +29,7 @@ struct DevSys {
   const int* blkidx;              // [nq][nkpt] global block of (q, k) with k <= k + q, else -1
   const double* kgq;              // [nkpt][npw_max] qhat.(k+G), Cartesian
   const float* xscale;            // [ng_max] sqrt(2 vbar(G) / (Omega Nk)), 0 at G = 0 and beyond ng0
+  const float* vsq;               // [nq][ng_max] sqrt(4 pi)/|q+G| (0 at q+G = 0 and beyond ngq)
   long long nblocks;
   int pair_variant;               // index of the pair-kernel variant chosen for this system, -1 = first valid
 };
@@ -60,6 +61,10 @@ int launch_pair_exchange(const DevSys& d, const void* u, void* rho_x, int* statu
 int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, int q_begin, int q_end, long long vbase,
                        int* status, void* stream);
 int launch_dipole(const DevSys& d, const void* coef, const double* energies, double gap_floor, void* P, void* stream);
+int launch_pair_chi0(const DevSys& d, const void* u, void* rho, int q_begin, int q_end, int* status, void* stream);
+size_t screen_ws_bytes(const DevSys& d, long long qchunk);
+int launch_screening(const DevSys& d, void* rho_chi, const double* energies, const void* P, int q_begin, int q_end,
+                     int iterations, void* W, float* residual, void* ws, double gap_floor, void* stream);
 int pair_supported(const DevSys& d);
 // Pair-kernel variants compiled for this system: writes up to cap (index, threads, rows, pmax, bmax, ppt,
 // merged) septets, returns the number valid; pair_variant_current returns the index pick() uses.

@@ -142,13 +142,35 @@ constexpr int kTQ = 8, kTK = 16;
 
 struct Job {
   int k, k2, a0, na, b0, nb, q, g0x, g0y, g0z;
-  int mode;             // 0 exchange (v x c), 1 vv', 2 cc', 3 vv' then cc'
+  int mode;             // 0 (v x c) products, 1 vv', 2 cc', 3 vv' then cc'
   float2* out_v;        // first output vector of the vv' (or exchange) products
   float2* out_c;        // first output vector of the cc' products
 };
 
 __device__ __forceinline__ bool decode_job(const DevSys& d, int mode, bool merged, int q0, int nqc, long long vbase,
                                            float2* out, Job& j) {
+  if (mode == 4) {                         // v at k, c at k' = fold(k + q), k + q = k' + G0 (all k)
+    const int qi = (int)(blockIdx.x / d.nkpt), k = (int)(blockIdx.x - (long long)qi * d.nkpt);
+    const int q = q0 + qi;
+    const int k1 = k / (d.nk2 * d.nk3), k2 = (k / d.nk3) % d.nk2, k3 = k % d.nk3;
+    const int q1 = q / (d.nk2 * d.nk3), q2 = (q / d.nk3) % d.nk2, q3 = q % d.nk3;
+    const int s1 = k1 + q1, s2 = k2 + q2, s3 = k3 + q3;
+    const int f1 = s1 % d.nk1, f2 = s2 % d.nk2, f3 = s3 % d.nk3;
+    j.k = k;
+    j.k2 = (f1 * d.nk2 + f2) * d.nk3 + f3;
+    j.q = q;
+    j.g0x = -(s1 / d.nk1);                 // sampled at G - g0 = G + G0
+    j.g0y = -(s2 / d.nk2);
+    j.g0z = -(s3 / d.nk3);
+    j.a0 = 0;
+    j.na = d.nv;
+    j.b0 = d.nv;
+    j.nb = d.nc;
+    j.mode = 0;
+    j.out_v = out + ((size_t)qi * d.nkpt + k) * d.nv * d.nc * d.ng_max;
+    j.out_c = nullptr;
+    return true;
+  }
   if (mode == 0) {
     j.k = j.k2 = blockIdx.x;
     j.a0 = 0;
@@ -612,6 +634,21 @@ int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, int q_begi
   if (int e = make_tmap(d, v, u, &tm)) return e;
   v->pair<<<(unsigned)cells, v->threads, sm, (cudaStream_t)stream>>>(d, (const float2*)u, (float2*)rho_dir, 1,
                                                                      q_begin, nqc, vbase, status, tm);
+  return (int)cudaGetLastError();
+}
+
+// rho_vc^{k,k+q}(G) for every k and q in [q_begin, q_end): rows ((q - q_begin) Nk + k) Nv Nc + v Nc + c.
+int launch_pair_chi0(const DevSys& d, const void* u, void* rho, int q_begin, int q_end, int* status, void* stream) {
+  const Variant* v = pick(d);
+  if (!v) return (int)cudaErrorInvalidValue;
+  const size_t sm = v->pair_smem(d.ng_max);
+  cudaFuncSetAttribute((const void*)v->pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const long long cells = (long long)(q_end - q_begin) * d.nkpt;
+  if (cells >= (1LL << 31)) return (int)cudaErrorInvalidValue;
+  CUtensorMap tm;
+  if (int e = make_tmap(d, v, u, &tm)) return e;
+  v->pair<<<(unsigned)cells, v->threads, sm, (cudaStream_t)stream>>>(d, (const float2*)u, (float2*)rho, 4, q_begin,
+                                                                     q_end - q_begin, 0, status, tm);
   return (int)cudaGetLastError();
 }
 

@@ -216,6 +216,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   std::vector<char4> h_gk((size_t)nkpt * npw_max, make_char4(0, 0, 0, 0));
   std::vector<int> h_npw(nkpt), h_ngq(nkpt);
   std::vector<double> h_kgq((size_t)nkpt * npw_max, 0.0);
+  std::vector<float> h_vsq((size_t)nkpt * ng_max, 0.0f);   // sqrt(4 pi)/|q+G| on the q spheres (= k spheres)
   for (int ik = 0; ik < nkpt; ++ik) {
     int o[3];
     offs(ik, o);
@@ -230,6 +231,8 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
         for (int j = 0; j < 3; ++j) kg[j] += red * b[i][j];
       }
       h_kgq[(size_t)ik * npw_max + t] = s.qhat[0] * kg[0] + s.qhat[1] * kg[1] + s.qhat[2] * kg[2];
+      const double kn = std::sqrt(kg[0] * kg[0] + kg[1] * kg[1] + kg[2] * kg[2]);
+      if (kn > 0.0 && t < ng_max) h_vsq[(size_t)ik * ng_max + t] = (float)(std::sqrt(4.0 * kPi) / kn);
     }
   }
   std::vector<int4> h_blocks(d.nblocks);
@@ -270,6 +273,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   const size_t o_kgq = off; off = align256(off + h_kgq.size() * sizeof(double));
   const size_t o_xs = off; off = align256(off + h_xs.size() * sizeof(float));
   const size_t o_bi = off; off = align256(off + h_blkidx.size() * sizeof(int));
+  const size_t o_vsq = off; off = align256(off + h_vsq.size() * sizeof(float));
   char* base = nullptr;
   bse_status st = cuda_check(cudaMalloc((void**)&base, off), "cudaMalloc(plan tables)");
   if (st != BSE_OK) return st;
@@ -286,6 +290,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   if (!err) err = up(o_kgq, h_kgq.data(), h_kgq.size() * sizeof(double));
   if (!err) err = up(o_xs, h_xs.data(), h_xs.size() * sizeof(float));
   if (!err) err = up(o_bi, h_blkidx.data(), h_blkidx.size() * sizeof(int));
+  if (!err) err = up(o_vsq, h_vsq.data(), h_vsq.size() * sizeof(float));
   if ((st = cuda_check(err, "cudaMemcpy(plan tables)")) != BSE_OK) return st;
   d.gk = (const char4*)(base + o_gk);
   d.npw = (const int*)(base + o_npw);
@@ -297,6 +302,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   d.kgq = (const double*)(base + o_kgq);
   d.xscale = (const float*)(base + o_xs);
   d.blkidx = (const int*)(base + o_bi);
+  d.vsq = (const float*)(base + o_vsq);
   return BSE_OK;
 }
 
@@ -429,6 +435,10 @@ bse_status bse_workspace_size(const bse_plan* plan, int s, int kind, long long a
       if (arg < 1) return set_error(BSE_ERR_ARG, "nsteps must be >= 1");
       *bytes = backward_ws_bytes(d, arg);
       return BSE_OK;
+    case BSE_WS_SCREEN:
+      if (arg < 1 || arg > d.nq) return set_error(BSE_ERR_ARG, "q chunk out of range");
+      *bytes = screen_ws_bytes(d, arg);
+      return BSE_OK;
   }
   return set_error(BSE_ERR_ARG, "unknown workspace kind");
 }
@@ -465,6 +475,14 @@ bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags, const void*
       if ((st = cuda_check(launch_dipole(d, coef, energies, sp.sys.gap_floor, P, stream), "dipole")) != BSE_OK)
         return st;
     }
+  }
+  if ((flags & BSE_PD_DIRECT) && (flags & BSE_PD_CHI0))
+    return set_error(BSE_ERR_ARG, "BSE_PD_DIRECT and BSE_PD_CHI0 both write rho_dir");
+  if (flags & BSE_PD_CHI0) {
+    if (!rho_dir || q_begin < 0 || q_end > d.nq || q_begin >= q_end) return set_error(BSE_ERR_ARG, "bad chi0 range");
+    if ((st = cuda_check(launch_pair_chi0(d, ws, rho_dir, q_begin, q_end, plan->d_status, stream), "pair chi0")) !=
+        BSE_OK)
+      return st;
   }
   if (flags & BSE_PD_DIRECT) {
     if (!rho_dir || q_begin < 0 || q_end > d.nq || q_begin >= q_end) return set_error(BSE_ERR_ARG, "bad direct range");
@@ -674,6 +692,24 @@ bse_status bse_spectrum_backward(bse_plan* plan, int s, const void* H, const voi
                                 plan->d_status, stream);
   if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "cooperative launch not possible on this device");
   return cuda_check(e, "spectrum backward");
+}
+
+bse_status bse_screening(bse_plan* plan, int s, void* rho_chi, const double* energies, const void* P, int q_begin,
+                         int q_end, int iterations, void* W, float* residual, void* ws, size_t ws_bytes,
+                         void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const SysPlan& sp = plan->sys[s];
+  const DevSys& d = sp.d;
+  if (sp.sys.coulomb != BSE_COULOMB_3D) return set_error(BSE_ERR_UNSUPPORTED, "screening is built for bulk systems");
+  if (!rho_chi || !energies || !W || q_begin < 0 || q_end > d.nq || q_begin >= q_end || iterations < 0 ||
+      iterations > 64)
+    return set_error(BSE_ERR_ARG, "bad screening arguments");
+  if (q_begin == 0 && !P) return set_error(BSE_ERR_ARG, "q = 0 needs the dipole P");
+  if (!ws || ws_bytes < screen_ws_bytes(d, q_end - q_begin)) return set_error(BSE_ERR_WORKSPACE, "workspace too small");
+  return cuda_check(launch_screening(d, rho_chi, energies, P, q_begin, q_end, iterations, W, residual, ws,
+                                     sp.sys.gap_floor, stream),
+                    "screening");
 }
 
 bse_status bse_set_wait_limit(unsigned long long ns) {
