@@ -246,6 +246,12 @@ def run_ours(args):
         step()       # restore the FP32 state
         torch.cuda.synchronize()
 
+    screening = None
+    if not args.no_screening and world == 1:
+        screening = run_screening(args, dev, spec, s, coef, en, F)
+        step()       # restore the step's own state
+        torch.cuda.synchronize()
+
     batch = None
     if not args.no_batch and world == 1:
         batch = run_batch(args, dev)
@@ -273,6 +279,7 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "mixed": mixed,
         "batch": batch,
+        "screening": screening,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(spec, s, budget_s=args.cpu_budget)
@@ -339,6 +346,53 @@ def run_batch(args, dev):
             "systems": len(specs), "dims": dims, "ms_per_batch": ms, "spectra_per_s": len(specs) / (ms / 1e3),
             "elements_per_s": float(sum(d * d for d in dims)) / (ms / 1e3), "pair_variants": tuned,
             "graph_replays_timed": reps}
+
+
+def run_screening(args, dev, spec, s, coef, en, F):
+    """Static RPA screening of the bench workload (all q): (k, k+q) pair densities, eps, Newton-Schulz
+    inverse, W.  Returns the summary for the JSON line (times by CUDA events)."""
+    import torch
+    from paper_1206_3518_gb300 import bse
+
+    plan = F.plan
+    inf = plan.info(0)
+    nq, ng, dim = inf["nq"], inf["ng_max"], inf["dim"]
+    iters = 16
+    rho = torch.empty(nq * dim, ng, dtype=torch.complex64, device=dev)
+    W = torch.empty(nq, ng, ng, dtype=torch.complex64, device=dev)
+    res = torch.empty(nq, dtype=torch.float32, device=dev)
+    ws = torch.empty(bse.bse_workspace_size(plan, 0, bse.BSE_WS_SCREEN, nq) // 8, dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def once(ev=None):
+        if ev:
+            ev[0].record(stream)
+        bse.bse_pair_densities(plan, 0, bse.BSE_PD_CHI0, None, None, None, None, rho, 0, nq, F.ws_pair)
+        if ev:
+            ev[1].record(stream)
+        bse.bse_screening(plan, 0, rho, en, F.P, 0, nq, iters, W, res, ws)
+        if ev:
+            ev[2].record(stream)
+
+    bse.bse_pair_densities(plan, 0, bse.BSE_PD_REALSPACE | bse.BSE_PD_EXCHANGE, coef, en, F.rho_x, F.P, None, 0, 0,
+                           F.ws_pair)
+    once()
+    torch.cuda.synchronize()
+    bse.bse_status_read(plan)
+    reps = 2
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(reps)]
+    for k in range(reps):
+        once(evs[k])
+    torch.cuda.synchronize()
+    bse.bse_status_read(plan)
+    t_pair = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    t_scr = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    ngq = [len(bse.bse_gvectors(plan, 0, q, 1)) for q in range(nq)]
+    flops = sum(8.0 * n * n * dim + iters * 2 * 8.0 * n ** 3 for n in ngq)     # eps GEMM + 2 GEMMs per iteration
+    return {"workload": f"{spec.name}, all {nq} q, {iters} Newton-Schulz steps",
+            "pair_chi0_ms": t_pair, "screening_ms": t_scr,
+            "screening_fp32_tflops": flops / (t_scr / 1e3) / 1e12,
+            "newton_schulz_residual_max": float(res.max().item())}
 
 
 def run_stage(args):
@@ -510,6 +564,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the BF16x3 comparison run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch of hexagonal sheets")
+    ap.add_argument("--no-screening", action="store_true", help="skip the static RPA screening measurement")
     ap.add_argument("--only", default="all", choices=["all", "pair", "spectrum", "contract"],
                     help="profiling aid: run one stage (pair: realspace + a q chunk of pair densities; "
                          "spectrum: Haydock on an H built once before the loop)")

@@ -24,7 +24,7 @@ def _dev(x, dtype):
     return torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
 
 
-def _run(bse, s, iterations=16):
+def _run(bse, s, iterations=16, keep_rho=True):
     from paper_1206_3518_gb300.pipeline import Forward
     spec = s.spec
     plan = bse.Plan([spec])
@@ -37,13 +37,13 @@ def _run(bse, s, iterations=16):
     rho = torch.zeros(nq * dim, ng, dtype=torch.complex64, device="cuda")
     bse.bse_pair_densities(plan, 0, bse.BSE_PD_CHI0, None, None, None, None, rho, 0, nq, F.ws_pair)
     bse.bse_status_read(plan)
-    rho_host = rho.cpu().numpy().copy()
+    rho_host = rho.cpu().numpy().copy().reshape(nq, dim, ng) if keep_rho else None
     W = torch.zeros(nq, ng, ng, dtype=torch.complex64, device="cuda")
     res = torch.zeros(nq, dtype=torch.float32, device="cuda")
     ws = torch.empty(bse.bse_workspace_size(plan, 0, bse.BSE_WS_SCREEN, nq) // 8, dtype=torch.complex64, device="cuda")
     bse.bse_screening(plan, 0, rho, en, F.P, 0, nq, iterations, W, res, ws)
     bse.bse_status_read(plan)
-    return plan, rho_host.reshape(nq, dim, ng), W.cpu().numpy(), res.cpu().numpy()
+    return plan, rho_host, W.cpu().numpy(), res.cpu().numpy()
 
 
 @pytest.mark.parametrize("which", ["tiny", "fcc_4x4x4_3v3c"])
@@ -63,3 +63,16 @@ def test_screening_matches_oracle(bse, tiny_spec, which):
         wg = W[iq][:ng, :ng]
         assert np.abs(wg - wref).max() < 1e-5 * np.abs(wref).max(), iq
         assert np.all(W[iq][ng:, :] == 0) and np.all(W[iq][:, ng:] == 0)
+
+
+def test_screening_fcc8_full_size_sampled(bse):
+    """fcc 8x8x8 3v4c (512 q, ng 314, K = 6144): W of q = 0 and two other q against the oracle."""
+    spec = config_spec("fcc_8x8x8_3v4c")
+    s = generate(spec, wdtype=np.complex64)
+    plan, _, W, res = _run(bse, s, keep_rho=False)
+    assert res.max() < 1e-5
+    P = op.dipole(spec, s.gk, s.coef, s.energies)
+    for iq in (0, 77, 300):
+        wref = scr.screened_w(spec, s, iq, P)
+        ng = wref.shape[0]
+        assert np.abs(W[iq][:ng, :ng] - wref).max() < 1e-5 * np.abs(wref).max(), iq
