@@ -72,6 +72,7 @@ typedef enum {
 #define BSE_PD_CHI0      8u   /* rho_vc^{k,k+q} for all k, q of a range (screening input) */
 #define BSE_BK_INIT      1u   /* A3 + A5 diagonal: H = diag + 2 K^x (upper)    */
 #define BSE_BK_DIRECT    2u   /* A4 + A5: H -= K^d for a q range, mirror       */
+#define BSE_BK_MIRROR    4u   /* A5 without A4: lower blocks and (B+B^H)/2      */
 
 /*
  * One periodic system.  Lattices: fcc with conventional constant a
@@ -182,6 +183,9 @@ bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags,
  * (rho_dir laid out as in bse_pair_densities for the same range) and writes the
  * mirrored lower block H_k'k = H_kk'^H; diagonal blocks become (B + B^H)/2.
  * After INIT and DIRECT over all q, H is the full Hermitian matrix.
+ * BSE_BK_MIRROR (not with DIRECT) completes an INIT-only build the same way: lower blocks
+ * H_k'k = H_kk'^H, diagonal blocks (B + B^H)/2.  INIT | MIRROR is the Tamm-Dancoff form of the
+ * random-phase response with local fields (exchange kernel only, no W).
  * W        complex64 [nq][ng_max][ng_max], W_q[p][p'] Hermitian, including 4 pi.
  * H        complex64 [dim][dim] row-major.
  * prec     BSE_PREC_FP32 (CUDA-core FP32) or BSE_PREC_BF16X3 (tcgen05 BF16

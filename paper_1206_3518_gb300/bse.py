@@ -21,7 +21,7 @@ BSE_COULOMB_3D, BSE_COULOMB_SLAB = 0, 1
 BSE_PREC_FP32, BSE_PREC_BF16X3 = 0, 1
 BSE_WS_PAIR, BSE_WS_KERNEL, BSE_WS_SPECTRUM, BSE_WS_BACKWARD, BSE_WS_SCREEN = 0, 1, 2, 3, 4
 BSE_PD_REALSPACE, BSE_PD_EXCHANGE, BSE_PD_DIRECT, BSE_PD_CHI0 = 1, 2, 4, 8
-BSE_BK_INIT, BSE_BK_DIRECT = 1, 2
+BSE_BK_INIT, BSE_BK_DIRECT, BSE_BK_MIRROR = 1, 2, 4
 
 EXPORTED = [
     "bse_last_error", "bse_plan_create", "bse_plan_create_host", "bse_plan_destroy", "bse_plan_info", "bse_gvectors",

@@ -244,7 +244,34 @@ __global__ __launch_bounds__(kBlkThreads) void block_kernel(DevSys d, const floa
   }
 }
 
+// Lower blocks from the upper ones, H_k'k = H_kk'^H, and diagonal blocks (B + B^H)/2 (for a build
+// without the direct term, which otherwise does this in its epilogue).
+__global__ void mirror_kernel(DevSys d, float2* __restrict__ H) {
+  const long long n = (long long)d.dim * d.dim;
+  const int nvc = d.nv * d.nc;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int S = (int)(i / d.dim), S2 = (int)(i - (long long)S * d.dim);
+    const int k = S / nvc, k2 = S2 / nvc;
+    if (k > k2) {
+      const float2 u = H[(size_t)S2 * d.dim + S];
+      H[i] = make_float2(u.x, -u.y);
+    } else if (k == k2 && S < S2) {
+      const float2 a = H[i], b = H[(size_t)S2 * d.dim + S];
+      const float2 m = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+      H[i] = m;
+      H[(size_t)S2 * d.dim + S] = make_float2(m.x, -m.y);
+    } else if (S == S2) {
+      H[i].y = 0.f;
+    }
+  }
+}
+
 }  // namespace
+
+int launch_mirror(const DevSys& d, void* H, void* stream) {
+  mirror_kernel<<<1216, 256, 0, (cudaStream_t)stream>>>(d, (float2*)H);
+  return (int)cudaGetLastError();
+}
 
 // FP32 W.rho rows of a q chunk, then (for BSE_PREC_BF16X3) the split BF16 tile images.
 static size_t x_bytes(const DevSys& d, long long qchunk) {

@@ -603,6 +603,10 @@ bse_status bse_build_kernel(bse_plan* plan, int s, unsigned flags, const void* r
     if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "precision not available in this build");
     if ((st = cuda_check(e, "kernel direct")) != BSE_OK) return st;
   }
+  if (flags & BSE_BK_MIRROR) {
+    if (flags & BSE_BK_DIRECT) return set_error(BSE_ERR_ARG, "the direct stage already mirrors its blocks");
+    if ((st = cuda_check(launch_mirror(d, H, stream), "kernel mirror")) != BSE_OK) return st;
+  }
   return BSE_OK;
 }
 
