@@ -83,6 +83,15 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def workload_config(spec, ng_max):
+    """The workload description shared by both arms of the bench."""
+    return {"workload": f"{spec.name}: fcc a=10 bohr, {spec.nk[0]}x{spec.nk[1]}x{spec.nk[2]} k, "
+                        f"{spec.nv}v{spec.nc}c, dim {spec.dim}, Ecut {spec.ecut} Ha (ng_max {ng_max}), grid "
+                        f"{spec.fft[0]}x{spec.fft[1]}x{spec.fft[2]}, {spec.nsteps} Haydock steps, {spec.nw} w",
+            "dim": spec.dim, "nblocks": spec.nkpt * (spec.nkpt + 1) // 2,
+            "l2": "inputs larger than L2 (u 0.94 GB, H 0.30 GB, W 0.40 GB); no flush"}
+
+
 def make_inputs(name):
     from synth import config_spec, generate
     import numpy as np
@@ -277,13 +286,11 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": world * dim * dim / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64 contractions, f64 recurrence" if prec == 0 else
-        "bf16x3 contractions, f64 recurrence", "data": "synthetic",
-        "config": {"workload": f"{spec.name}: fcc a=10 bohr, 8x8x8 k, 3v4c, dim {dim}, Ecut 8.6 Ha "
-                               f"(ng_max {inf['ng_max']}), grid 32^3, {spec.nsteps} Haydock steps, {spec.nw} w",
-                   "dim": dim, "nblocks": inf["nblocks"], "precision": args.prec,
-                   "l2": "inputs larger than L2 (u 0.94 GB, H 0.30 GB, W 0.40 GB); no flush",
-                   "parallelism": f"replicas x{world}"},
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(spec, inf["ng_max"]),
+                       precision=("complex64 (f32) contractions" if prec == 0 else "bf16x3 contractions") +
+                       ", f64 Lanczos coefficients and continued fraction",
+                       parallelism=f"replicas x{world}"),
         "stages_ms": stage_ms,
         "kernel_elements_per_s": dim * dim / ((ms_per_step - stage_ms["spectrum"]) / 1e3),
         "spectra_per_s": 1e3 / stage_ms["spectrum"],
@@ -557,10 +564,13 @@ def run_reference(args):
         base = cpu_baseline(spec, s, budget_s=args.cpu_budget)
         if k >= args.warmup:
             times.append(time.perf_counter() - t0)
-    out = {"metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+    from oracle import geometry as geo
+    ng_max = max(len(geo.sphere(spec, tuple(o))) for o in geo.mesh_offsets(spec))
+    out = {"metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": base["est_step_s"] * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
-           "config": {"workload": f"{spec.name} (oracle, bounded sample per step)"},
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": dict(workload_config(spec, ng_max), precision="complex128 oracle (CPU), bounded sample per step",
+                          parallelism="host cores"),
            "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "sample": base["sample"], "value": base["value"]},
            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
