@@ -154,3 +154,36 @@ def test_grid_variant_full_parity(bse, name):
     assert np.abs(Hg - H)[off].max() / np.abs(H[off]).max() < 1e-5
     ref = osp.eps2_haydock(spec, H, Pv, s.omega, spec.eta, spec.nsteps)[0]
     assert np.abs(eps - ref).max() / ref.max() < 1e-5
+
+
+def test_fcc12_mixed_precision_sampled(bse):
+    """fcc 12x12x12 4v4c (dim 27648): BF16x3 tensor-core build against the oracle on sampled blocks
+    (max and mean relative error of the kernel entries) and its eps_2 against the FP32 build's (the
+    FP32 build is itself checked against the oracle above); tolerance 1e-3 of the eps_2 peak."""
+    from paper_1206_3518_gb300.pipeline import Forward
+    s = generate(config_spec("fcc_12x12x12_4v4c"), wdtype=np.complex64)
+    spec = s.spec
+    plan = bse.Plan([spec])
+    nsteps = 60
+    F = Forward(plan, 0, nsteps=nsteps, nw=len(s.omega), qchunk=96)
+    coef, en, W = _dev(s.coef, torch.complex64), _dev(s.energies, torch.float64), _dev(s.W, torch.complex64)
+    om = _dev(s.omega, torch.float64)
+    F.build(coef, en, W, spec.delta, bse.BSE_PREC_FP32)
+    e32 = F.spectrum(om, spec.eta, nsteps).cpu().numpy().copy()
+    F.build(coef, en, W, spec.delta, bse.BSE_PREC_BF16X3)
+    ebf = F.spectrum(om, spec.eta, nsteps).cpu().numpy().copy()
+    bse.bse_status_read(plan)
+    assert np.abs(ebf - e32).max() / e32.max() < 1e-3
+    rng = np.random.default_rng(12)
+    nvc = spec.nv * spec.nc
+    errs, scale = [], 0.0
+    for ik, ik2 in [(0, 0)] + [tuple(sorted(rng.integers(0, spec.nkpt, 2))) for _ in range(12)]:
+        ref, _ = _oracle_block(spec, s, ik, ik2, spec.delta)
+        got = F.H[ik * nvc:(ik + 1) * nvc, ik2 * nvc:(ik2 + 1) * nvc].cpu().numpy()
+        off = ~np.eye(nvc, dtype=bool) if ik == ik2 else np.ones((nvc, nvc), bool)
+        errs.append(np.abs(got - ref)[off].ravel())
+        scale = max(scale, np.abs(ref[off]).max())
+    err = np.concatenate(errs) / scale
+    print(f"fcc12 BF16x3 kernel entries: max {err.max():.2e}, mean {err.mean():.2e} of the largest; "
+          f"eps_2 vs FP32 {np.abs(ebf - e32).max() / e32.max():.2e}")
+    assert err.max() < 1e-3 and err.mean() < 1e-4
