@@ -83,6 +83,29 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x, world, device="cpu"):
+    """The largest x over the ranks of the default process group (x itself for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard_systems(dims, rank, world):
+    """Indices of the systems rank owns: largest dim^2 first, each to the least-loaded rank (ties: lower
+    rank).  Every rank computes the same assignment; no exchange is needed."""
+    load = [0.0] * world
+    owner = [0] * len(dims)
+    for i in sorted(range(len(dims)), key=lambda i: (-dims[i] * dims[i], i)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        owner[i] = r
+        load[r] += float(dims[i]) * dims[i]
+    return [i for i in range(len(dims)) if owner[i] == rank]
+
+
 def workload_config(spec, ng_max):
     """The workload description shared by both arms of the bench."""
     return {"workload": f"{spec.name}: fcc a=10 bohr, {spec.nk[0]}x{spec.nk[1]}x{spec.nk[2]} k, "
@@ -183,10 +206,7 @@ def run_ours(args):
     ms = t0.elapsed_time(t1)
     stage_ms = {n: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, n in enumerate(ev_names)}
     bse.bse_status_read(plan)
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks(ms, world, dev)
     ms_per_step = ms / args.steps
 
     # end to end through host buffers: inputs H2D from pinned memory, eps_2 D2H, every step.  The screening
@@ -276,8 +296,8 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     batch = None
-    if not args.no_batch and world == 1:
-        batch = run_batch(args, dev)
+    if not args.no_batch:
+        batch = run_batch(args, dev, rank, world)
 
     peaks, src = _peaks()
     # dominant stage: by measured time
@@ -310,17 +330,21 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_batch(args, dev):
+def run_batch(args, dev, rank=0, world=1):
     """Layered 2D batch: 16 hexagonal sheets (dims 576..20736), BF16x3 contractions, autotuned pair tiles,
     per-system builds plus one batched persistent spectrum launch, the whole sequence replayed as one
-    CUDA graph.  Returns the summary for the JSON line."""
+    CUDA graph.  With several ranks the sheets are sharded (balanced by dim^2, no exchange) and the time
+    is the slowest rank's.  Returns the summary for the JSON line."""
     import numpy as np
     import torch
+    import torch.distributed as dist
     from paper_1206_3518_gb300 import autotune, bse
     from paper_1206_3518_gb300.pipeline import Batch
     from synth import generate, slab_batch_specs
 
-    specs = slab_batch_specs(0)
+    all_specs = slab_batch_specs(0)
+    mine = shard_systems([sp.dim for sp in all_specs], rank, world)
+    specs = [all_specs[i] for i in mine]
     systems = [generate(sp, wdtype=np.complex64) for sp in specs]
     plan = bse.Plan(specs)
     nsteps, nw = specs[0].nsteps, specs[0].nw
@@ -354,18 +378,24 @@ def run_batch(args, dev):
     reps = max(1, min(args.steps, 3))
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
     e0.record(stream)
     for _ in range(reps):
         g.replay()
     e1.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     bse.bse_status_read(plan)
-    ms = e0.elapsed_time(e1) / reps
-    dims = [sp.dim for sp in specs]
+    ms = max_over_ranks(e0.elapsed_time(e1) / reps, world, dev)
+    dims = [sp.dim for sp in all_specs]
     return {"workload": "16 hexagonal sheets (a 4.7, c 30 bohr, slab Coulomb), k meshes 24x24..48x48, 1-3 v and c "
-                        "bands, 300 steps, 2000 w; BF16x3 contractions; one CUDA graph per batch",
-            "systems": len(specs), "dims": dims, "ms_per_batch": ms, "spectra_per_s": len(specs) / (ms / 1e3),
-            "elements_per_s": float(sum(d * d for d in dims)) / (ms / 1e3), "pair_variants": tuned,
+                        "bands, 300 steps, 2000 w; BF16x3 contractions; one CUDA graph per batch and rank",
+            "systems": len(all_specs), "dims": dims, "ms_per_batch": ms,
+            "spectra_per_s": len(all_specs) / (ms / 1e3),
+            "elements_per_s": float(sum(d * d for d in dims)) / (ms / 1e3),
+            "pair_variants_rank0": tuned, "ranks": world, "scaling": "strong" if world > 1 else None,
             "graph_replays_timed": reps}
 
 
