@@ -158,8 +158,11 @@ def test_ragged_small_systems(bse, nk, nv, nc):
 
 
 def test_breakdown_reports_fewer_steps(bse):
-    """nsteps = dim on a 9-dim system: the recursion completes exactly (no spurious breakdown),
-    and a kernel-off system with degenerate transitions breaks down early and exactly."""
+    """nsteps = dim on a 27-dim system: the recursion matches the oracle's step count and spectrum.
+    With the kernel off (rho_x = 0, no direct term) H is diagonal with two distinct transition
+    energies: the Krylov space of P closes after two vectors (up to the FP32 rounding of the
+    matrix-vector product, ~1e-7 |H v|, below the 1e-6 breakdown threshold), so the recursion must
+    stop after exactly two steps and reproduce the closed-form independent-particle spectrum."""
     spec = SystemSpec("brk", "fcc", 10.0, 0.0, (3, 3, 3), 1, 1, 1.0, (8, 8, 8), "3d", nsteps=27, nw=100)
     s = generate(spec)
     e = s.energies.copy()
@@ -167,10 +170,7 @@ def test_breakdown_reports_fewer_steps(bse):
     e[:, 1] = np.where(np.arange(27) % 2 == 0, 0.2, 0.3)     # two distinct transition energies
     s.energies = e
     s.W[:] = 0.0
-    s.coef = s.coef.copy()
     plan, F = _forward(bse, s, 27)
-    # remove exchange by zeroing rho_x before the H build is not possible through the ABI; use W = 0 and check
-    # that P lies in an invariant subspace only when the kernel vanishes -> compare against oracle instead.
     om = _dev(s.omega, torch.float64)
     eps = F.spectrum(om, spec.eta, nsteps=27).cpu().numpy()
     rx = op.exchange_rho(spec, s.gk, s.coef)
@@ -180,3 +180,40 @@ def test_breakdown_reports_fewer_steps(bse):
     ref, _, _, done = osp.eps2_haydock(spec, H, P, s.omega, spec.eta, 27)
     assert int(F.steps_done.item()) == done
     assert np.abs(eps - ref).max() / ref.max() < 1e-5
+    # kernel off
+    e1 = s.energies
+    en = _dev(e1, torch.float64)
+    F.rho_x.zero_()
+    bse.bse_build_kernel(plan, 0, bse.BSE_BK_INIT | bse.BSE_BK_MIRROR, F.rho_x, None, 0, 0, None, en, spec.delta,
+                         bse.BSE_PREC_FP32, F.H, None)
+    eps0 = F.spectrum(om, spec.eta, nsteps=27).cpu().numpy()
+    bse.bse_status_read(plan)
+    assert int(F.steps_done.item()) == 2
+    de = ok.transition_energies(spec, e1, spec.delta)
+    ip = osp.eps2_independent(spec, de, P, s.omega, spec.eta)
+    assert np.abs(eps0 - ip).max() / ip.max() < 1e-5
+
+
+def test_error_returns_on_a_device_plan(bse, tiny_spec):
+    """Invalid ranges, step counts and workspaces are refused before any launch."""
+    from paper_1206_3518_gb300.pipeline import Forward
+    plan = bse.Plan([tiny_spec])
+    F = Forward(plan, 0, nsteps=8, nw=16)
+    om = torch.zeros(16, dtype=torch.float64, device="cuda")
+    cases = [
+        (lambda: bse.bse_pair_densities(plan, 0, bse.BSE_PD_DIRECT, None, None, None, None, F.rho_dir, 3, 3,
+                                        F.ws_pair), bse.BSE_ERR_ARG),
+        (lambda: bse.bse_pair_densities(plan, 0, bse.BSE_PD_DIRECT, None, None, None, None, F.rho_dir, 0, 1,
+                                        F.ws_pair[:16]), bse.BSE_ERR_WORKSPACE),
+        (lambda: bse.bse_spectrum(plan, 0, F.H, F.P, 0, om, 0.01, F.eps2[:16], F.ab, F.steps_done, F.ws_spec),
+         bse.BSE_ERR_ARG),
+        (lambda: bse.bse_build_kernel(plan, 0, bse.BSE_BK_DIRECT | bse.BSE_BK_MIRROR, None, F.rho_dir, 0, 1,
+                                      F.rho_x, None, 0.0, bse.BSE_PREC_FP32, F.H, F.ws_kernel), bse.BSE_ERR_ARG),
+        (lambda: bse.bse_build_kernel(plan, 0, bse.BSE_BK_DIRECT, None, F.rho_dir, 0, 1, F.rho_x, None, 0.0, 7,
+                                      F.H, F.ws_kernel), bse.BSE_ERR_ARG),
+    ]
+    for call, code in cases:
+        with pytest.raises(bse.BseError) as err:
+            call()
+        assert err.value.code == code
+    bse.bse_status_read(plan)
