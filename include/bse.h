@@ -49,7 +49,8 @@ typedef enum {
   BSE_ERR_NONFINITE = 3,    /* NaN/Inf found in an input scan */
   BSE_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
   BSE_ERR_UNSUPPORTED = 5,  /* configuration outside the compiled kernels */
-  BSE_ERR_WORKSPACE = 6     /* workspace smaller than bse_workspace_size */
+  BSE_ERR_WORKSPACE = 6,    /* workspace smaller than bse_workspace_size */
+  BSE_ERR_INDEFINITE = 7    /* coupled spectrum: F H2 not positive definite (unstable system) or P = 0 */
 } bse_status;
 
 typedef enum { BSE_LATTICE_FCC = 0, BSE_LATTICE_HEX = 1 } bse_lattice;
@@ -62,7 +63,9 @@ typedef enum {
   BSE_WS_KERNEL = 1,    /* bse_build_kernel: W.rho products of one q chunk */
   BSE_WS_SPECTRUM = 2,  /* bse_spectrum: Krylov basis, vectors, partial sums */
   BSE_WS_BACKWARD = 3,  /* bse_spectrum_backward: basis, dL/dH, chain products */
-  BSE_WS_SCREEN = 4     /* bse_screening: dielectric matrices of one q chunk (arg = chunk) */
+  BSE_WS_SCREEN = 4,    /* bse_screening: dielectric matrices of one q chunk (arg = chunk) */
+  BSE_WS_COUPLING = 5,  /* bse_build_coupling: W.rho_cv' of one q chunk (arg = chunk; 0 = INIT only) */
+  BSE_WS_COUPLED = 6    /* bse_spectrum_coupled: basis, vectors, partial sums (arg = nsteps) */
 } bse_ws_kind;
 
 /* Stage flags for bse_pair_densities and bse_build_kernel. */
@@ -70,9 +73,13 @@ typedef enum {
 #define BSE_PD_EXCHANGE  2u   /* A2 exchange set rho_x and the A6 dipole P     */
 #define BSE_PD_DIRECT    4u   /* A2 direct set rho_vv', rho_cc' of a q range   */
 #define BSE_PD_CHI0      8u   /* rho_vc^{k,k+q} for all k, q of a range (screening input) */
+#define BSE_PD_COUPLING 16u   /* rho_vc', rho_cv' of the upper blocks of a q range (coupling) */
 #define BSE_BK_INIT      1u   /* A3 + A5 diagonal: H = diag + 2 K^x (upper)    */
 #define BSE_BK_DIRECT    2u   /* A4 + A5: H -= K^d for a q range, mirror       */
 #define BSE_BK_MIRROR    4u   /* A5 without A4: lower blocks and (B+B^H)/2      */
+#define BSE_BC_INIT      1u   /* coupling: B = 2 Bx (upper block triangle)       */
+#define BSE_BC_DIRECT    2u   /* coupling: B -= Bd for a q range, mirror B^T     */
+#define BSE_BC_MIRROR    4u   /* coupling without Bd: lower blocks, (B+B^T)/2    */
 
 /*
  * One periodic system.  Lattices: fcc with conventional constant a
@@ -166,7 +173,9 @@ bse_status bse_rho_dir_count(const bse_plan* plan, int s, int q_begin, int q_end
  *          nblk_q*nc*nc vectors rho~_cc'^{kk'}; entry p is taken at G = g_p(q) - G0,
  *          g_p the p-th vector of the q sphere, so q_unf + G = q + g_p.
  * flags    BSE_PD_* stages; REALSPACE must run (once) before the others, with
- *          the same workspace.  Unused outputs may be NULL.
+ *          the same workspace.  Unused outputs may be NULL.  With BSE_PD_COUPLING (not with
+ *          DIRECT or CHI0) rho_dir receives the coupling densities of bse_build_coupling,
+ *          bse_rho_cpl_count(q_begin, q_end) vectors.
  * Errors: BSE_ERR_ARG (range, NULL for a requested output), BSE_ERR_WORKSPACE.
  */
 bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags,
@@ -333,6 +342,62 @@ bse_status bse_autotune_pair(bse_plan* plan, int s, void* ws, size_t ws_bytes, v
 bse_status bse_screening(bse_plan* plan, int s, void* rho_chi, const double* energies, const void* P, int q_begin,
                          int q_end, int iterations, void* W, float* residual, void* ws, size_t ws_bytes,
                          void* stream);
+
+/*
+ * The BSE beyond the Tamm-Dancoff approximation (Appendix A): e-h pairs S = (k, v, c) coupled to
+ * h-e pairs (k, c -> v).  In the basis (e-h, h-e) the Hamiltonian is
+ *   H2 = [[A, B], [-conj(B), -conj(A)]],
+ * A the Tamm-Dancoff H of bse_build_kernel, B the coupling block below.
+ *
+ * Number of complex vectors of rho_cpl for q in [q_begin, q_end) (each ng_max long):
+ * 2 Nv Nc per upper block.
+ */
+bse_status bse_rho_cpl_count(const bse_plan* plan, int s, int q_begin, int q_end, long long* nvec);
+
+/*
+ * Coupling block B = 2 Bx - Bd (Eqs. V_eh and W_SS with the band labels of the h-e pair):
+ *   Bx_SS' = 1/(Omega Nk) sum_{G != 0} conj(rho_vc^{kk}(G)) vbar(G) conj(rho_v'c'^{k'k'}(-G)),
+ *   Bd_SS' = 1/(Omega Nk) sum_{G,G'} conj(rho_vc'^{kk'}(G)) W_GG'(k'-k) rho_cv'^{kk'}(G').
+ * B is symmetric (B^T = B) for W with the reciprocity W_{-G,-G'}(-q) = conj(W_GG'(q)).
+ * rho_x    as in bse_pair_densities (BSE_PD_EXCHANGE).
+ * rho_cpl  complex64 [nvec][ng_max] from bse_pair_densities with BSE_PD_COUPLING (rho_dir
+ *          argument) for the same q range: per q, nblk_q Nv Nc vectors rho~_vc'^{kk'}
+ *          (block-major, then v, c'), then nblk_q Nc Nv vectors rho~_cv'^{kk'} (block-major,
+ *          then c, v'), with the G = g_p(q) - G0 convention of rho_dir.
+ * BSE_BC_INIT writes 2 Bx on the upper block triangle (k <= k'); BSE_BC_DIRECT subtracts Bd for
+ * the upper blocks of q in [q_begin, q_end) and writes the mirror B_k'k = B_kk'^T (diagonal blocks
+ * (B + B^T)/2); BSE_BC_MIRROR (not with DIRECT) completes an INIT-only build the same way.
+ * Bm       complex64 [dim][dim] row-major.  W, prec as in bse_build_kernel.
+ * ws       bse_workspace_size(BSE_WS_COUPLING, q_end - q_begin) bytes (0 for INIT alone).
+ * Errors: BSE_ERR_ARG, BSE_ERR_WORKSPACE, BSE_ERR_UNSUPPORTED (Nv Nc > 16, or a q = 0 sphere
+ * without its -G partners).
+ */
+bse_status bse_build_coupling(bse_plan* plan, int s, unsigned flags, const void* rho_x, const void* rho_cpl,
+                              int q_begin, int q_end, const void* W, int prec, void* Bm, void* ws, size_t ws_bytes,
+                              void* stream);
+
+/*
+ * eps_2 of the coupled problem (Eqs. Dyson_eh_rearrange and epsilon_chi_bar with f = diag(1, -1)):
+ *   eps_2(w) = -C Im[Pt^H (z - H2)^{-1} F Pt],  Pt = (P, -conj P),  F = diag(1, -1),  z = w + i eta,
+ * the h-e optical element being -conj(P).  Evaluated by Lanczos on H2 in the inner product of
+ * M = F H2 (Hermitian; positive definite for a stable system) from s = F Pt, which gives
+ *   eps_2 = -C b_0^2 Im[g(z)/z],  g(z) = 1/(z - b_1^2/(z - b_2^2/(...))),  b_0 = |s|_M;
+ * the diagonal coefficients vanish by the e-h / h-e symmetry, and the recursion runs on the e-h
+ * halves of the Lanczos vectors (one product with A and one with B per step; full
+ * reorthogonalisation, twice, against the vectors of the same parity).
+ * A, Bm    complex64 [dim][dim] (A Hermitian, Bm symmetric; full matrices).
+ * P        complex128 [dim].  omega float64 [nw] (Ha).  nsteps in [1, 2 dim].
+ * eps2     float64 [nw];  b float64 [nsteps]: b_0 = |s|_M, b_1..b_{n-1};  steps_done int32 [1]:
+ *          fewer than nsteps after a breakdown (|w_j|_M <= 1e-6 |H2 q_{j-1}|_M), not an error.
+ * ws       bse_workspace_size(BSE_WS_COUPLED, nsteps) bytes.
+ * A negative squared M-norm (M not positive definite), or P = 0, stops the recursion and sets
+ * BSE_ERR_INDEFINITE in the plan's status word (read with bse_status_read).  4 kernels per step,
+ * no device-side waits; capturable in a CUDA graph.
+ * Errors: BSE_ERR_ARG, BSE_ERR_WORKSPACE, BSE_ERR_UNSUPPORTED (dim > 65536).
+ */
+bse_status bse_spectrum_coupled(bse_plan* plan, int s, const void* A, const void* Bm, const void* P, int nsteps,
+                                const double* omega, int nw, double eta, double* eps2, double* b, int* steps_done,
+                                void* ws, size_t ws_bytes, void* stream);
 
 /*
  * Failure injection: limit (ns) of every grid-barrier wait of the spectrum kernels (steps A7,

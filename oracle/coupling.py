@@ -183,9 +183,9 @@ def m_lanczos(A, B, P, nsteps):
     dim = len(P)
     F = f_sign(dim)
 
-    def apply(x):                                 # H2 x from the blocks
+    def apply(x):                                 # H2 x from the blocks; conj(M) y = conj(M conj(y))
         top, bot = x[:dim], x[dim:]
-        return np.concatenate([A @ top + B @ bot, -(np.conj(B) @ top) - np.conj(A) @ bot])
+        return np.concatenate([A @ top + B @ bot, -np.conj(B @ np.conj(top) + A @ np.conj(bot))])
 
     nsteps = min(nsteps, 2 * dim)
     s = F * p_tilde(P)
@@ -207,7 +207,7 @@ def m_lanczos(A, B, P, nsteps):
             break
         w = p - a[j] * q - (b[j] * Q[j - 1] if j > 0 else 0.0)
         for _ in range(2):
-            h = np.conj(MQ[: j + 1]) @ w
+            h = np.conj(MQ[: j + 1] @ np.conj(w))       # (M q_i)^H w for every i <= j
             w = w - Q[: j + 1].T @ h
         u = apply(w)
         beta2 = np.vdot(w, F * u).real

@@ -16,18 +16,22 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libbse.so")
 
 BSE_OK, BSE_ERR_ARG, BSE_ERR_CUDA, BSE_ERR_NONFINITE, BSE_ERR_TIMEOUT, BSE_ERR_UNSUPPORTED, BSE_ERR_WORKSPACE = range(7)
+BSE_ERR_INDEFINITE = 7
 BSE_LATTICE_FCC, BSE_LATTICE_HEX = 0, 1
 BSE_COULOMB_3D, BSE_COULOMB_SLAB = 0, 1
 BSE_PREC_FP32, BSE_PREC_BF16X3 = 0, 1
 BSE_WS_PAIR, BSE_WS_KERNEL, BSE_WS_SPECTRUM, BSE_WS_BACKWARD, BSE_WS_SCREEN = 0, 1, 2, 3, 4
-BSE_PD_REALSPACE, BSE_PD_EXCHANGE, BSE_PD_DIRECT, BSE_PD_CHI0 = 1, 2, 4, 8
+BSE_WS_COUPLING, BSE_WS_COUPLED = 5, 6
+BSE_PD_REALSPACE, BSE_PD_EXCHANGE, BSE_PD_DIRECT, BSE_PD_CHI0, BSE_PD_COUPLING = 1, 2, 4, 8, 16
 BSE_BK_INIT, BSE_BK_DIRECT, BSE_BK_MIRROR = 1, 2, 4
+BSE_BC_INIT, BSE_BC_DIRECT, BSE_BC_MIRROR = 1, 2, 4
 
 EXPORTED = [
     "bse_last_error", "bse_plan_create", "bse_plan_create_host", "bse_plan_destroy", "bse_plan_info", "bse_gvectors",
     "bse_pair_blocks", "bse_workspace_size", "bse_rho_dir_count", "bse_pair_densities",
     "bse_build_kernel", "bse_apply_H", "bse_spectrum", "bse_spectrum_static", "bse_spectrum_batch", "bse_spectrum_backward", "bse_status_read",
     "bse_pair_variants", "bse_set_pair_variant", "bse_autotune_pair", "bse_set_wait_limit", "bse_screening",
+    "bse_rho_cpl_count", "bse_build_coupling", "bse_spectrum_coupled",
 ]
 
 
@@ -95,6 +99,9 @@ def load():
     lib.bse_screening.argtypes = [vp, i, vp, vp, vp, i, i, i, vp, vp, vp, sz, vp]
     lib.bse_autotune_pair.argtypes = [vp, i, vp, sz, vp, i, i, i, ctypes.POINTER(ctypes.c_float), i,
                                       ctypes.POINTER(i), vp]
+    lib.bse_rho_cpl_count.argtypes = [vp, i, i, i, ctypes.POINTER(ll)]
+    lib.bse_build_coupling.argtypes = [vp, i, u, vp, vp, i, i, vp, i, vp, vp, sz, vp]
+    lib.bse_spectrum_coupled.argtypes = [vp, i, vp, vp, vp, i, vp, i, d, vp, vp, vp, vp, sz, vp]
     for name in EXPORTED:
         if name != "bse_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -298,3 +305,22 @@ def bse_screening(plan, s, rho_chi, energies, P, q_begin, q_end, iterations, W, 
     """Static RPA W of q in [q_begin, q_end) from BSE_PD_CHI0 pair densities (rho_chi is overwritten)."""
     _check(load().bse_screening(plan.handle, s, _ptr(rho_chi), _ptr(energies), _ptr(P), q_begin, q_end,
                                 int(iterations), _ptr(W), _ptr(residual), _ptr(ws), _nbytes(ws), _stream()))
+
+
+def bse_rho_cpl_count(plan, s, q_begin, q_end) -> int:
+    n = ctypes.c_longlong()
+    _check(load().bse_rho_cpl_count(plan.handle, s, q_begin, q_end, ctypes.byref(n)))
+    return int(n.value)
+
+
+def bse_build_coupling(plan, s, flags, rho_x, rho_cpl, q_begin, q_end, W, prec, Bm, ws):
+    """Coupling block B = 2 Bx - Bd of the BSE beyond the Tamm-Dancoff approximation."""
+    _check(load().bse_build_coupling(plan.handle, s, flags, _ptr(rho_x), _ptr(rho_cpl), q_begin, q_end, _ptr(W),
+                                     int(prec), _ptr(Bm), _ptr(ws), _nbytes(ws), _stream()))
+
+
+def bse_spectrum_coupled(plan, s, A, Bm, P, nsteps, omega, eta, eps2, b, steps_done, ws):
+    """eps_2 of H2 = [[A, B], [-conj B, -conj A]] by Lanczos in the F H2 inner product."""
+    _check(load().bse_spectrum_coupled(plan.handle, s, _ptr(A), _ptr(Bm), _ptr(P), int(nsteps), _ptr(omega),
+                                       omega.numel(), float(eta), _ptr(eps2), _ptr(b), _ptr(steps_done), _ptr(ws),
+                                       _nbytes(ws), _stream()))

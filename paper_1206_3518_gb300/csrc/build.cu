@@ -17,6 +17,7 @@
 
 #include "gemm_tile.cuh"
 #include "internal.h"
+#include "layout.cuh"
 
 namespace bse {
 namespace {
@@ -77,13 +78,11 @@ __global__ __launch_bounds__(wr::kThreads, 2) void gemm_wr(DevSys d, const float
   const int q = q_begin + blockIdx.z;
   const long long b0 = d.qblk_off[q_begin];
   const long long nblk = d.qblk_off[q + 1] - d.qblk_off[q];
-  const int w = side_c ? d.nc * d.nc : d.nv * d.nv;
+  const int w = side_width(d, side_c);
   const int M = (int)(nblk * w), NG = d.ngq[q];
   const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
   if (m0 >= M || n0 >= NG) return;
-  long long aoff = d.qvec_off[q] - vbase;
-  if (side_c) aoff += nblk * d.nv * d.nv;
-  const float2* A = rho_dir + (size_t)aoff * d.ng_max;
+  const float2* A = rho_dir + (size_t)side_rows_offset(d, q, side_c, vbase) * d.ng_max;
   const float2* B = W + (size_t)q * d.ng_max * d.ng_max;
   float2* C = X + (size_t)((d.qblk_off[q] - b0) * w) * d.ng_max;
   __shared__ __align__(16) Smem sm;
@@ -266,6 +265,132 @@ __global__ void mirror_kernel(DevSys d, float2* __restrict__ H) {
   }
 }
 
+// ---------------------------------------------------------------- coupling block B (Appendix A)
+//
+// B_SS' = 2 Bx_SS' - Bd_SS' couples the e-h pair S = (k, v, c) with the h-e pair (k', c' -> v'):
+//   Bx_SS' = (1/(Omega Nk)) sum_{G != 0} conj(rho_vc^{kk}(G)) vbar(G) conj(rho_v'c'^{k'k'}(-G))
+//   Bd_SS' = (1/(Omega Nk)) sum_{G,G'} conj(rho_vc'^{kk'}(G)) W_GG'(q) rho_cv'^{kk'}(G')
+// B is symmetric: the upper blocks k <= k' are built and mirrored as B_k'k = B_kk'^T.
+
+// rhot[S][G] = conj(rho_x[S][-G]) on the q = 0 sphere (the h-e pair density).
+__global__ void minus_g_kernel(DevSys d, const float2* __restrict__ rho_x, float2* __restrict__ rhot) {
+  const long long n = (long long)d.dim * d.ng0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int S = (int)(i / d.ng0), t = (int)(i - (long long)S * d.ng0);
+    const int m = d.gminus0[t];
+    const float2 v = m >= 0 ? rho_x[(size_t)S * d.ng_max + m] : make_float2(0.f, 0.f);
+    rhot[(size_t)S * d.ng_max + t] = make_float2(v.x, -v.y);
+  }
+}
+
+// B = 2 Bx on tiles touching k(S) <= k(S') (the exchange scale sqrt(2 vbar/(Omega Nk)) on both operands).
+__global__ __launch_bounds__(kGemmThreads) void cpl_init_kernel(DevSys d, const float2* __restrict__ rho_x,
+                                                                const float2* __restrict__ rhot,
+                                                                float2* __restrict__ Bm) {
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  if (m0 >= d.dim || n0 >= d.dim) return;
+  if (kpt_of_pair(d, m0) > kpt_of_pair(d, min(n0 + BN, d.dim) - 1)) return;
+  __shared__ gemm::Smem sm;
+  float2 acc[4][4];
+  gemm::tile<true, true, true, false, true>(rho_x, d.ng_max, d.dim, rhot, d.ng_max, d.dim, d.ng0, m0, n0, sm, acc,
+                                            d.xscale);
+  const int tm = threadIdx.x / 16, tn = threadIdx.x % 16;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int S = m0 + tm * 4 + i;
+    if (S >= d.dim) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int S2 = n0 + tn * 4 + j;
+      if (S2 < d.dim) Bm[(size_t)S * d.dim + S2] = acc[i][j];
+    }
+  }
+}
+
+// Per upper block: M[a][c] = sum_G conj(Lv[a][G]) X[c][G], a = (v, c'), c = (c, v'), X = W rho_cv';
+// B[(k,v,c)][(k',v',c')] -= M/(Omega Nk), mirror B_k'k = B_kk'^T, diagonal blocks (B + B^T)/2.
+__global__ __launch_bounds__(kBlkThreads) void cpl_block_kernel(DevSys d, const float2* __restrict__ rho_cpl,
+                                                               const float2* __restrict__ X, float2* __restrict__ Bm,
+                                                               int q_begin, long long vbase) {
+  __shared__ float2 Ls[16][KC + 1];
+  __shared__ float2 Rs[16][KC + 1];
+  __shared__ float2 Bs[16][17];
+  const long long b0 = d.qblk_off[q_begin];
+  const long long b = b0 + blockIdx.x;
+  const int4 blk = d.blocks[b];
+  const int k = blk.x, k2 = blk.y, q = blk.z;
+  const long long qb = d.qblk_off[q];
+  const long long local = b - qb;
+  const int nv = d.nv, nc = d.nc, w = nv * nc;
+  const float2* L = rho_cpl + (size_t)(2LL * w * qb - vbase + local * w) * d.ng_max;
+  const float2* R = X + (size_t)((qb - b0 + local) * w) * d.ng_max;
+  const int NG = d.ngq[q];
+  const int t = threadIdx.x;
+  const int a = t / w, c = t % w;
+  const bool active = t < w * w;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int g0 = 0; g0 < NG; g0 += KC) {
+    for (int i = t; i < 16 * KC; i += kBlkThreads) {
+      const int r = i / KC, g = i % KC;
+      const bool in = r < w && (g0 + g) < NG;
+      Ls[r][g] = in ? L[(size_t)r * d.ng_max + g0 + g] : make_float2(0.f, 0.f);
+      Rs[r][g] = in ? R[(size_t)r * d.ng_max + g0 + g] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll 8
+      for (int g = 0; g < KC; ++g) {
+        const float2 l = Ls[a][g], r = Rs[c][g];
+        acc.x = fmaf(l.x, r.x, fmaf(l.y, r.y, acc.x));     // conj(l) r
+        acc.y = fmaf(l.x, r.y, fmaf(-l.y, r.x, acc.y));
+      }
+    }
+    __syncthreads();
+  }
+  const float nrm = (float)d.norm;
+  int row = 0, col = 0;
+  float2 val = make_float2(0.f, 0.f);
+  if (active) {
+    const int v = a / nc, cp = a % nc, cc = c / nv, vp = c % nv;
+    row = v * nc + cc;                 // (k, v, c) local
+    col = vp * nc + cp;                // (k', v', c') local
+    const size_t bij = (size_t)(k * w + row) * d.dim + (size_t)k2 * w + col;
+    const float2 h = Bm[bij];
+    val = make_float2(h.x - nrm * acc.x, h.y - nrm * acc.y);
+    if (k != k2) {
+      Bm[bij] = val;
+      Bm[(size_t)(k2 * w + col) * d.dim + (size_t)k * w + row] = val;
+    } else {
+      Bs[row][col] = val;
+    }
+  }
+  if (k == k2) {
+    __syncthreads();
+    if (active) {
+      const float2 o = Bs[col][row];
+      Bm[(size_t)(k * w + row) * d.dim + (size_t)k * w + col] = make_float2(0.5f * (val.x + o.x), 0.5f * (val.y + o.y));
+    }
+  }
+}
+
+// Lower blocks B_k'k = B_kk'^T and diagonal blocks (B + B^T)/2 for a build without the direct term.
+__global__ void cpl_mirror_kernel(DevSys d, float2* __restrict__ Bm) {
+  const long long n = (long long)d.dim * d.dim;
+  const int nvc = d.nv * d.nc;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int S = (int)(i / d.dim), S2 = (int)(i - (long long)S * d.dim);
+    const int k = S / nvc, k2 = S2 / nvc;
+    if (k > k2) {
+      Bm[i] = Bm[(size_t)S2 * d.dim + S];
+    } else if (k == k2 && S < S2) {
+      const float2 a = Bm[i], b = Bm[(size_t)S2 * d.dim + S];
+      const float2 m = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
+      Bm[i] = m;
+      Bm[(size_t)S2 * d.dim + S] = m;
+    }
+  }
+}
+
 }  // namespace
 
 int launch_mirror(const DevSys& d, void* H, void* stream) {
@@ -273,15 +398,29 @@ int launch_mirror(const DevSys& d, void* H, void* stream) {
   return (int)cudaGetLastError();
 }
 
-// FP32 W.rho rows of a q chunk, then (for BSE_PREC_BF16X3) the split BF16 tile images.
-static size_t x_bytes(const DevSys& d, long long qchunk) {
-  const long long w = (d.nv * d.nv <= d.nc * d.nc) ? d.nv * d.nv : d.nc * d.nc;
+// FP32 W.rho rows of a q chunk (w rows per block), then (for BSE_PREC_BF16X3) the split BF16 tile images.
+static size_t x_bytes(const DevSys& d, long long qchunk, long long w) {
   long long nb = qchunk * d.nkpt;
   if (nb > d.nblocks) nb = d.nblocks;
   return (((size_t)(nb * w) * d.ng_max * sizeof(float2)) + 255) & ~(size_t)255;
 }
 
-size_t kernel_ws_bytes(const DevSys& d, long long qchunk) { return x_bytes(d, qchunk) + tc_split_bytes(d, qchunk); }
+static long long direct_width(const DevSys& d) {
+  return (d.nv * d.nv <= d.nc * d.nc) ? d.nv * d.nv : d.nc * d.nc;
+}
+
+size_t kernel_ws_bytes(const DevSys& d, long long qchunk) {
+  const long long w = direct_width(d);
+  return x_bytes(d, qchunk, w) + tc_split_bytes(d, qchunk, w);
+}
+
+// Coupling build: W.rho_cv' rows and split images of a q chunk, or (init) conj(rho_x(-G)) rows.
+size_t coupling_ws_bytes(const DevSys& d, long long qchunk) {
+  const long long w = (long long)d.nv * d.nc;
+  const size_t direct = qchunk > 0 ? x_bytes(d, qchunk, w) + tc_split_bytes(d, qchunk, w) : 0;
+  const size_t init = (((size_t)d.dim * d.ng_max * sizeof(float2)) + 255) & ~(size_t)255;
+  return direct > init ? direct : init;
+}
 
 int launch_kernel_init(const DevSys& d, const void* rho_x, const double* energies, double delta, void* H,
                        void* stream) {
@@ -305,7 +444,7 @@ int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin
   cudaStream_t st = (cudaStream_t)stream;
   int e;
   if (prec == BSE_PREC_BF16X3) {
-    void* split_ws = (char*)ws + x_bytes(d, q_end - q_begin);
+    void* split_ws = (char*)ws + x_bytes(d, q_end - q_begin, direct_width(d));
     e = launch_gemm_wr_tc(d, rho_dir, q_begin, q_end, vbase, max_rows, W, ws, split_ws, side_c, status, stream);
   } else if (prec == BSE_PREC_FP32) {
     dim3 grid((d.ng_max + wr::TN - 1) / wr::TN, (unsigned)((max_rows + wr::TM - 1) / wr::TM), q_end - q_begin);
@@ -319,6 +458,43 @@ int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin
   if (b_count > 0)
     block_kernel<<<(unsigned)b_count, kBlkThreads, 0, st>>>(d, (const float2*)rho_dir, (const float2*)ws, (float2*)H,
                                                             q_begin, vbase, side_c);
+  return (int)cudaGetLastError();
+}
+
+int launch_coupling_init(const DevSys& d, const void* rho_x, void* Bm, void* ws, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  minus_g_kernel<<<1216, 256, 0, st>>>(d, (const float2*)rho_x, (float2*)ws);
+  dim3 grid((d.dim + BN - 1) / BN, (d.dim + BM - 1) / BM);
+  cpl_init_kernel<<<grid, kGemmThreads, 0, st>>>(d, (const float2*)rho_x, (const float2*)ws, (float2*)Bm);
+  return (int)cudaGetLastError();
+}
+
+int launch_coupling_mirror(const DevSys& d, void* Bm, void* stream) {
+  cpl_mirror_kernel<<<1216, 256, 0, (cudaStream_t)stream>>>(d, (float2*)Bm);
+  return (int)cudaGetLastError();
+}
+
+int launch_coupling_direct_range(const DevSys& d, const void* rho_cpl, int q_begin, int q_end, long long b_count,
+                                 long long vbase, long long max_rows, const void* W, int prec, void* Bm, void* ws,
+                                 int* status, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long w = (long long)d.nv * d.nc;
+  int e;
+  if (prec == BSE_PREC_BF16X3) {
+    void* split_ws = (char*)ws + x_bytes(d, q_end - q_begin, w);
+    e = launch_gemm_wr_tc(d, rho_cpl, q_begin, q_end, vbase, max_rows, W, ws, split_ws, 2, status, stream);
+  } else if (prec == BSE_PREC_FP32) {
+    dim3 grid((d.ng_max + wr::TN - 1) / wr::TN, (unsigned)((max_rows + wr::TM - 1) / wr::TM), q_end - q_begin);
+    gemm_wr<<<grid, wr::kThreads, 0, st>>>(d, (const float2*)rho_cpl, (const float2*)W, (float2*)ws, q_begin, vbase,
+                                           2);
+    e = (int)cudaGetLastError();
+  } else {
+    return -1;
+  }
+  if (e) return e;
+  if (b_count > 0)
+    cpl_block_kernel<<<(unsigned)b_count, kBlkThreads, 0, st>>>(d, (const float2*)rho_cpl, (const float2*)ws,
+                                                                (float2*)Bm, q_begin, vbase);
   return (int)cudaGetLastError();
 }
 

@@ -32,6 +32,7 @@ struct DevSys {
   const float* vsq;               // [nq][ng_max] sqrt(4 pi)/|q+G| (0 at q+G = 0 and beyond ngq)
   long long nblocks;
   int pair_variant;               // index of the pair-kernel variant chosen for this system, -1 = first valid
+  const int* gminus0;             // [ng0] index of -G on the q = 0 sphere (-1 if absent)
 };
 
 struct SysPlan {
@@ -40,6 +41,7 @@ struct SysPlan {
   std::vector<std::vector<int32_t>> gk, gq;   // host spheres, flattened (g1,g2,g3)*
   std::vector<int32_t> blocks;                 // host (ik, ik2, iq, g0x, g0y, g0z) per block
   std::vector<long long> qblk_off, qvec_off;
+  bool gminus0_complete = false;  // every G of the q = 0 sphere has -G on it
   void* dmem = nullptr;           // one device allocation holding every table
 };
 
@@ -79,7 +81,20 @@ int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin
 int launch_gemm_wr_tc(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long vbase,
                       long long max_rows, const void* W, void* X, void* split_ws, int side_c, int* status,
                       void* stream);
-size_t tc_split_bytes(const DevSys& d, long long qchunk);
+size_t tc_split_bytes(const DevSys& d, long long qchunk, long long w);
+// Coupling block B of the BSE beyond the Tamm-Dancoff approximation (build.cu, coupled.cu).
+int launch_pair_coupling(const DevSys& d, const void* u, void* rho_cpl, int q_begin, int q_end, long long vbase,
+                         int* status, void* stream);
+size_t coupling_ws_bytes(const DevSys& d, long long qchunk);
+int launch_coupling_init(const DevSys& d, const void* rho_x, void* Bm, void* ws, void* stream);
+int launch_coupling_direct_range(const DevSys& d, const void* rho_cpl, int q_begin, int q_end, long long b_count,
+                                 long long vbase, long long max_rows, const void* W, int prec, void* Bm, void* ws,
+                                 int* status, void* stream);
+int launch_coupling_mirror(const DevSys& d, void* Bm, void* stream);
+size_t coupled_ws_bytes(const DevSys& d, long long nsteps);
+int launch_spectrum_coupled(const DevSys& d, const void* A, const void* Bm, const void* P, int nsteps,
+                            const double* omega, int nw, double eta, double* eps2, double* b, int* steps_done,
+                            void* ws, int* status, void* stream);
 size_t kernel_ws_bytes(const DevSys& d, long long qchunk);
 int launch_gemm_wr(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long vbase, long long max_rows,
                    const void* W, void* X, int side_c, void* stream);

@@ -142,10 +142,21 @@ constexpr int kTQ = 8, kTK = 16;
 
 struct Job {
   int k, k2, a0, na, b0, nb, q, g0x, g0y, g0z;
-  int mode;             // 0 (v x c) products, 1 vv', 2 cc', 3 vv' then cc'
-  float2* out_v;        // first output vector of the vv' (or exchange) products
-  float2* out_c;        // first output vector of the cc' products
+  int mode;             // 0 (v x c) products, 1 vv', 2 cc', 3 vv' then cc';
+                        // coupling: 5 vc' then cv', 6 vc', 7 cv'
+  float2* out_v;        // first output vector of the vv' (exchange, vc') products
+  float2* out_c;        // first output vector of the cc' (cv') products
 };
+
+__device__ __forceinline__ int nprod(const DevSys& d, int mode) {
+  switch (mode) {
+    case 0: case 6: case 7: return d.nv * d.nc;
+    case 1: return d.nv * d.nv;
+    case 2: return d.nc * d.nc;
+    case 5: return 2 * d.nv * d.nc;
+    default: return d.nv * d.nv + d.nc * d.nc;
+  }
+}
 
 __device__ __forceinline__ bool decode_job(const DevSys& d, int mode, bool merged, int q0, int nqc, long long vbase,
                                            float2* out, Job& j) {
@@ -209,6 +220,30 @@ __device__ __forceinline__ bool decode_job(const DevSys& d, int mode, bool merge
   const long long qb = d.qblk_off[q];
   const long long nblk = d.qblk_off[q + 1] - qb;
   const long long local = b - qb;
+  if (mode == 5) {                         // coupling densities: per q [nblk][Nv Nc] vc', then [nblk][Nc Nv] cv'
+    const long long w = (long long)d.nv * d.nc;
+    const long long cbase = 2 * w * qb - vbase;
+    j.out_v = out + (size_t)(cbase + local * w) * d.ng_max;
+    j.out_c = out + (size_t)(cbase + nblk * w + local * w) * d.ng_max;
+    if (merged) {
+      j.mode = 5;
+      j.a0 = j.b0 = 0;
+      j.na = j.nb = d.nb;
+    } else if (group == 0) {               // v at k, c at k'
+      j.mode = 6;
+      j.a0 = 0;
+      j.na = d.nv;
+      j.b0 = d.nv;
+      j.nb = d.nc;
+    } else {                               // c at k, v at k'
+      j.mode = 7;
+      j.a0 = d.nv;
+      j.na = d.nc;
+      j.b0 = 0;
+      j.nb = d.nv;
+    }
+    return true;
+  }
   const long long base = d.qvec_off[q] - vbase;
   j.out_v = out + (size_t)(base + local * d.nv * d.nv) * d.ng_max;
   j.out_c = out + (size_t)(base + nblk * d.nv * d.nv + local * d.nc * d.nc) * d.ng_max;
@@ -242,6 +277,25 @@ __device__ __forceinline__ void product_of(const DevSys& d, const Job& j, int p,
   } else if (j.mode == 2) {                // (c, c')
     sa = p / nc;
     sb = j.na + p % nc;
+    dst = j.out_c + (size_t)p * d.ng_max;
+  } else if (j.mode == 5) {                // merged coupling: (v, c') then (c, v'); slabs hold all nb bands
+    if (p < nv * nc) {
+      sa = p / nc;
+      sb = j.na + nv + p % nc;
+      dst = j.out_v + (size_t)p * d.ng_max;
+    } else {
+      const int t = p - nv * nc;
+      sa = nv + t / nv;
+      sb = j.na + t % nv;
+      dst = j.out_c + (size_t)t * d.ng_max;
+    }
+  } else if (j.mode == 6) {                // (v at k, c' at k')
+    sa = p / nc;
+    sb = j.na + p % nc;
+    dst = j.out_v + (size_t)p * d.ng_max;
+  } else if (j.mode == 7) {                // (c at k, v' at k')
+    sa = p / nv;
+    sb = j.na + p % nv;
     dst = j.out_c + (size_t)p * d.ng_max;
   } else if (p < nv * nv) {                // merged: (v, v') then (c, c'); slabs hold all nb bands
     sa = p / nv;
@@ -318,9 +372,7 @@ __global__ __launch_bounds__(THREADS, 1) void pair_kernel(DevSys d, const float2
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  const int P = (jb.mode == 0) ? d.nv * d.nc
-              : (jb.mode == 1) ? d.nv * d.nv
-              : (jb.mode == 2) ? d.nc * d.nc : d.nv * d.nv + d.nc * d.nc;
+  const int P = nprod(d, jb.mode);
   const int NG = d.ngq[jb.q];
   for (int t = tid; t < NG; t += THREADS) {
     const char4 g = d.gq[(size_t)jb.q * d.ng_max + t];
@@ -633,6 +685,25 @@ int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, int q_begi
   CUtensorMap tm;
   if (int e = make_tmap(d, v, u, &tm)) return e;
   v->pair<<<(unsigned)cells, v->threads, sm, (cudaStream_t)stream>>>(d, (const float2*)u, (float2*)rho_dir, 1,
+                                                                     q_begin, nqc, vbase, status, tm);
+  return (int)cudaGetLastError();
+}
+
+// Coupling densities rho_vc'^{kk'} and rho_cv'^{kk'} of the upper blocks of [q_begin, q_end) (same
+// job tiling as the direct set; nv^2 + nc^2 >= 2 nv nc, so every variant valid there fits these).
+int launch_pair_coupling(const DevSys& d, const void* u, void* rho_cpl, int q_begin, int q_end, long long vbase,
+                         int* status, void* stream) {
+  const Variant* v = pick(d);
+  if (!v) return (int)cudaErrorInvalidValue;
+  const size_t sm = v->pair_smem(d.ng_max);
+  cudaFuncSetAttribute((const void*)v->pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int nqc = q_end - q_begin;
+  const long long ntk = (d.nkpt + kTK - 1) / kTK, ntq = (nqc + kTQ - 1) / kTQ;
+  const long long cells = ntq * ntk * kTQ * kTK * (v->merged ? 1 : 2);
+  if (cells >= (1LL << 31)) return (int)cudaErrorInvalidValue;
+  CUtensorMap tm;
+  if (int e = make_tmap(d, v, u, &tm)) return e;
+  v->pair<<<(unsigned)cells, v->threads, sm, (cudaStream_t)stream>>>(d, (const float2*)u, (float2*)rho_cpl, 5,
                                                                      q_begin, nqc, vbase, status, tm);
   return (int)cudaGetLastError();
 }

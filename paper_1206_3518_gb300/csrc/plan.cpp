@@ -15,6 +15,7 @@
 #include <cstring>
 #include <string>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -262,6 +263,20 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
     h_xs[t] = (float)std::sqrt(2.0 * d.norm * v);
   }
 
+  // -G on the q = 0 sphere (coupling exchange, Bx)
+  std::vector<int> h_gm0(d.ng0 > 0 ? d.ng0 : 1, -1);
+  {
+    std::unordered_map<long long, int> pos;
+    auto key = [](int a, int b2, int c) { return ((long long)(a + 512) << 20) | ((long long)(b2 + 512) << 10) | (c + 512); };
+    for (int t = 0; t < d.ng0; ++t) pos[key(sp.gq[0][3 * t], sp.gq[0][3 * t + 1], sp.gq[0][3 * t + 2])] = t;
+    sp.gminus0_complete = true;
+    for (int t = 0; t < d.ng0; ++t) {
+      auto it = pos.find(key(-sp.gq[0][3 * t], -sp.gq[0][3 * t + 1], -sp.gq[0][3 * t + 2]));
+      if (it == pos.end()) sp.gminus0_complete = false;
+      else h_gm0[t] = it->second;
+    }
+  }
+
   if (!device) return BSE_OK;
   size_t off = 0;
   const size_t o_gk = off; off = align256(off + h_gk.size() * sizeof(char4));
@@ -274,6 +289,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   const size_t o_xs = off; off = align256(off + h_xs.size() * sizeof(float));
   const size_t o_bi = off; off = align256(off + h_blkidx.size() * sizeof(int));
   const size_t o_vsq = off; off = align256(off + h_vsq.size() * sizeof(float));
+  const size_t o_gm0 = off; off = align256(off + h_gm0.size() * sizeof(int));
   char* base = nullptr;
   bse_status st = cuda_check(cudaMalloc((void**)&base, off), "cudaMalloc(plan tables)");
   if (st != BSE_OK) return st;
@@ -291,6 +307,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   if (!err) err = up(o_xs, h_xs.data(), h_xs.size() * sizeof(float));
   if (!err) err = up(o_bi, h_blkidx.data(), h_blkidx.size() * sizeof(int));
   if (!err) err = up(o_vsq, h_vsq.data(), h_vsq.size() * sizeof(float));
+  if (!err) err = up(o_gm0, h_gm0.data(), h_gm0.size() * sizeof(int));
   if ((st = cuda_check(err, "cudaMemcpy(plan tables)")) != BSE_OK) return st;
   d.gk = (const char4*)(base + o_gk);
   d.npw = (const int*)(base + o_npw);
@@ -303,6 +320,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   d.xscale = (const float*)(base + o_xs);
   d.blkidx = (const int*)(base + o_bi);
   d.vsq = (const float*)(base + o_vsq);
+  d.gminus0 = (const int*)(base + o_gm0);
   return BSE_OK;
 }
 
@@ -439,6 +457,14 @@ bse_status bse_workspace_size(const bse_plan* plan, int s, int kind, long long a
       if (arg < 1 || arg > d.nq) return set_error(BSE_ERR_ARG, "q chunk out of range");
       *bytes = screen_ws_bytes(d, arg);
       return BSE_OK;
+    case BSE_WS_COUPLING:
+      if (arg < 0 || arg > d.nq) return set_error(BSE_ERR_ARG, "q chunk out of range");
+      *bytes = coupling_ws_bytes(d, arg);
+      return BSE_OK;
+    case BSE_WS_COUPLED:
+      if (arg < 1) return set_error(BSE_ERR_ARG, "nsteps < 1");
+      *bytes = coupled_ws_bytes(d, arg);
+      return BSE_OK;
   }
   return set_error(BSE_ERR_ARG, "unknown workspace kind");
 }
@@ -476,8 +502,15 @@ bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags, const void*
         return st;
     }
   }
-  if ((flags & BSE_PD_DIRECT) && (flags & BSE_PD_CHI0))
-    return set_error(BSE_ERR_ARG, "BSE_PD_DIRECT and BSE_PD_CHI0 both write rho_dir");
+  if (((flags & BSE_PD_DIRECT) != 0) + ((flags & BSE_PD_CHI0) != 0) + ((flags & BSE_PD_COUPLING) != 0) > 1)
+    return set_error(BSE_ERR_ARG, "BSE_PD_DIRECT, BSE_PD_CHI0 and BSE_PD_COUPLING all write rho_dir");
+  if (flags & BSE_PD_COUPLING) {
+    if (!rho_dir || q_begin < 0 || q_end > d.nq || q_begin >= q_end) return set_error(BSE_ERR_ARG, "bad coupling range");
+    const long long vb = 2LL * d.nv * d.nc * sp.qblk_off[q_begin];
+    if ((st = cuda_check(launch_pair_coupling(d, ws, rho_dir, q_begin, q_end, vb, plan->d_status, stream),
+                         "pair coupling")) != BSE_OK)
+      return st;
+  }
   if (flags & BSE_PD_CHI0) {
     if (!rho_dir || q_begin < 0 || q_end > d.nq || q_begin >= q_end) return set_error(BSE_ERR_ARG, "bad chi0 range");
     if ((st = cuda_check(launch_pair_chi0(d, ws, rho_dir, q_begin, q_end, plan->d_status, stream), "pair chi0")) !=
@@ -714,6 +747,69 @@ bse_status bse_screening(bse_plan* plan, int s, void* rho_chi, const double* ene
   return cuda_check(launch_screening(d, rho_chi, energies, P, q_begin, q_end, iterations, W, residual, ws,
                                      sp.sys.gap_floor, stream),
                     "screening");
+}
+
+bse_status bse_rho_cpl_count(const bse_plan* plan, int s, int q_begin, int q_end, long long* nvec) {
+  bse_status st = check_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const SysPlan& sp = plan->sys[s];
+  if (!nvec || q_begin < 0 || q_end > sp.d.nq || q_begin > q_end) return set_error(BSE_ERR_ARG, "bad q range");
+  *nvec = 2LL * sp.d.nv * sp.d.nc * (sp.qblk_off[q_end] - sp.qblk_off[q_begin]);
+  return BSE_OK;
+}
+
+bse_status bse_build_coupling(bse_plan* plan, int s, unsigned flags, const void* rho_x, const void* rho_cpl,
+                              int q_begin, int q_end, const void* W, int prec, void* Bm, void* ws, size_t ws_bytes,
+                              void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const SysPlan& sp = plan->sys[s];
+  const DevSys& d = sp.d;
+  if (!Bm) return set_error(BSE_ERR_ARG, "Bm is NULL");
+  if (prec != BSE_PREC_FP32 && prec != BSE_PREC_BF16X3) return set_error(BSE_ERR_ARG, "unknown precision");
+  if (d.nv * d.nc > 16) return set_error(BSE_ERR_UNSUPPORTED, "coupling blocks are built for Nv Nc <= 16");
+  if ((flags & BSE_BC_DIRECT) && (flags & BSE_BC_MIRROR))
+    return set_error(BSE_ERR_ARG, "the direct stage already mirrors its blocks");
+  if (flags & BSE_BC_INIT) {
+    if (!rho_x) return set_error(BSE_ERR_ARG, "init needs rho_x");
+    if (!sp.gminus0_complete) return set_error(BSE_ERR_UNSUPPORTED, "q = 0 sphere is not symmetric under G -> -G");
+    if (!ws || ws_bytes < coupling_ws_bytes(d, 0)) return set_error(BSE_ERR_WORKSPACE, "coupling workspace too small");
+    if ((st = cuda_check(launch_coupling_init(d, rho_x, Bm, ws, stream), "coupling init")) != BSE_OK) return st;
+  }
+  if (flags & BSE_BC_DIRECT) {
+    if (!rho_cpl || !W || q_begin < 0 || q_end > d.nq || q_begin >= q_end)
+      return set_error(BSE_ERR_ARG, "direct stage needs rho_cpl, W and a q range");
+    if (!ws || ws_bytes < coupling_ws_bytes(d, q_end - q_begin))
+      return set_error(BSE_ERR_WORKSPACE, "coupling workspace too small");
+    const long long w = (long long)d.nv * d.nc;
+    const long long nb = sp.qblk_off[q_end] - sp.qblk_off[q_begin], vb = 2 * w * sp.qblk_off[q_begin];
+    long long max_rows = 0;
+    for (int q = q_begin; q < q_end; ++q) max_rows = std::max(max_rows, (sp.qblk_off[q + 1] - sp.qblk_off[q]) * w);
+    const int e = launch_coupling_direct_range(d, rho_cpl, q_begin, q_end, nb, vb, max_rows, W, prec, Bm, ws,
+                                               plan->d_status, stream);
+    if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "precision not available in this build");
+    if ((st = cuda_check(e, "coupling direct")) != BSE_OK) return st;
+  }
+  if (flags & BSE_BC_MIRROR) {
+    if ((st = cuda_check(launch_coupling_mirror(d, Bm, stream), "coupling mirror")) != BSE_OK) return st;
+  }
+  return BSE_OK;
+}
+
+bse_status bse_spectrum_coupled(bse_plan* plan, int s, const void* A, const void* Bm, const void* P, int nsteps,
+                                const double* omega, int nw, double eta, double* eps2, double* b, int* steps_done,
+                                void* ws, size_t ws_bytes, void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const DevSys& d = plan->sys[s].d;
+  if (!A || !Bm || !P || !omega || !eps2 || !b || !steps_done || nsteps < 1 || nw < 0 || !(eta > 0.0))
+    return set_error(BSE_ERR_ARG, "coupled spectrum needs A, Bm, P, omega, eps2, b, steps_done, nsteps >= 1, eta > 0");
+  if (nsteps > 2 * d.dim) return set_error(BSE_ERR_ARG, "nsteps > 2 dim");
+  if (!ws || ws_bytes < coupled_ws_bytes(d, nsteps)) return set_error(BSE_ERR_WORKSPACE, "coupled workspace too small");
+  const int e = launch_spectrum_coupled(d, A, Bm, P, nsteps, omega, nw, eta, eps2, b, steps_done, ws, plan->d_status,
+                                        stream);
+  if (e == -2) return set_error(BSE_ERR_UNSUPPORTED, "coupled spectrum is built for dim <= 65536");
+  return cuda_check(e, "coupled spectrum");
 }
 
 bse_status bse_set_wait_limit(unsigned long long ns) {

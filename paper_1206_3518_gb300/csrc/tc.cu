@@ -26,6 +26,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "layout.cuh"
 
 namespace bse {
 namespace {
@@ -153,12 +154,10 @@ __global__ __launch_bounds__(kTcThreads) void split_a_kernel(DevSys d, const flo
   const int c = blockIdx.x, mt = blockIdx.y, qi = blockIdx.z;
   const int q = g.q_begin + qi;
   const long long nblk = d.qblk_off[q + 1] - d.qblk_off[q];
-  const int w = g.side_c ? d.nc * d.nc : d.nv * d.nv;
+  const int w = side_width(d, g.side_c);
   const int M = (int)(nblk * w), NG = d.ngq[q];
   if (mt * TM >= M || c * TKC >= NG) return;
-  long long aoff = d.qvec_off[q] - g.vbase;
-  if (g.side_c) aoff += nblk * d.nv * d.nv;
-  const float2* A = rho_dir + (size_t)aoff * d.ng_max;
+  const float2* A = rho_dir + (size_t)side_rows_offset(d, q, g.side_c, g.vbase) * d.ng_max;
   unsigned char* hi = As + a_tile_off(g, qi, mt, c);
   for (int it = threadIdx.x; it < TM * 4; it += kTcThreads) {
     const int r = it >> 2, cq = it & 3;
@@ -244,7 +243,7 @@ __global__ __launch_bounds__(kTcThreads, 1) void tc_gemm_wr(DevSys d, TcArgs a) 
 
   const SplitGeo& g = a.g;
   const int N = g.n_tile;
-  const int w = g.side_c ? d.nc * d.nc : d.nv * d.nv;
+  const int w = side_width(d, g.side_c);
   const long long b0 = d.qblk_off[g.q_begin];
   const long long ntiles = (long long)g.nq * g.mt_max * g.nt_max;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -437,8 +436,7 @@ int tc_n_tile(const DevSys& d) {
 
 }  // namespace
 
-size_t tc_split_bytes(const DevSys& d, long long qchunk) {
-  const long long w = (d.nv * d.nv <= d.nc * d.nc) ? d.nv * d.nv : d.nc * d.nc;
+size_t tc_split_bytes(const DevSys& d, long long qchunk, long long w) {
   const int N = tc_n_tile(d);
   const long long mt = (d.nkpt * w + TM - 1) / TM, nt = (d.ng_max + N - 1) / N;
   const long long kc = (d.ng_max + TKC - 1) / TKC;

@@ -66,6 +66,48 @@ class Forward:
         return self.eps2[: omega.numel()]
 
 
+class Coupled:
+    """Buffers and call sequence of the BSE with e-h / h-e coupling for the system of ``fwd``.
+
+    The resonant block A is ``fwd.H``; ``build`` needs the real-space wavefunctions and rho_x that
+    ``fwd.build`` leaves in place.  The coupling densities are streamed over ``fwd.chunks``.
+    """
+
+    def __init__(self, fwd: Forward, nsteps: int | None = None, nw: int | None = None):
+        self.fwd = fwd
+        plan, s = fwd.plan, fwd.s
+        dev = fwd.H.device
+        self.nsteps = fwd.nsteps if nsteps is None else nsteps
+        nvec = max(bse.bse_rho_cpl_count(plan, s, a, b) for a, b in fwd.chunks)
+        self.rho_cpl = torch.zeros(nvec, fwd.ng_max, dtype=torch.complex64, device=dev)
+        self.ws = torch.empty(bse.bse_workspace_size(plan, s, bse.BSE_WS_COUPLING, fwd.qchunk) // 8 + 1,
+                              dtype=torch.complex64, device=dev)
+        self.ws_spec = torch.empty(bse.bse_workspace_size(plan, s, bse.BSE_WS_COUPLED, self.nsteps) // 8 + 1,
+                                   dtype=torch.complex64, device=dev)
+        self.Bm = torch.empty(fwd.dim, fwd.dim, dtype=torch.complex64, device=dev)
+        self.eps2 = torch.zeros(fwd.eps2.numel() if nw is None else nw, dtype=torch.float64, device=dev)
+        self.b = torch.zeros(self.nsteps, dtype=torch.float64, device=dev)
+        self.steps_done = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def build(self, W, prec=bse.BSE_PREC_FP32):
+        """Coupling block B = 2 Bx - Bd (exchange from rho_x, direct term streamed over q chunks)."""
+        f = self.fwd
+        p, s = f.plan, f.s
+        bse.bse_build_coupling(p, s, bse.BSE_BC_INIT, f.rho_x, None, 0, 0, None, prec, self.Bm, self.ws)
+        for q0, q1 in f.chunks:
+            bse.bse_pair_densities(p, s, bse.BSE_PD_COUPLING, None, None, None, None, self.rho_cpl, q0, q1, f.ws_pair)
+            bse.bse_build_coupling(p, s, bse.BSE_BC_DIRECT, None, self.rho_cpl, q0, q1, W, prec, self.Bm, self.ws)
+        return self.Bm
+
+    def spectrum(self, omega, eta, nsteps=None):
+        """eps_2 of H2 = [[A, B], [-conj B, -conj A]] with A = fwd.H."""
+        n = self.nsteps if nsteps is None else nsteps
+        f = self.fwd
+        bse.bse_spectrum_coupled(f.plan, f.s, f.H, self.Bm, f.P, n, omega, eta, self.eps2[: omega.numel()], self.b,
+                                 self.steps_done, self.ws_spec)
+        return self.eps2[: omega.numel()]
+
+
 class Batch:
     """Several systems of one plan: per-system builds (q-streamed) and one batched spectrum launch."""
 
