@@ -295,11 +295,15 @@ def run_ours(args):
         step()       # restore the step's own state
         torch.cuda.synchronize()
 
+    peaks, src = _peaks()
+    coupled = None
+    if not args.no_coupled and world == 1:
+        coupled = run_coupled(args, dev, spec, W, om, F, peaks)
+
     batch = None
     if not args.no_batch:
         batch = run_batch(args, dev, rank, world)
 
-    peaks, src = _peaks()
     # dominant stage: by measured time
     dom = max(stage_ms, key=stage_ms.get)
     roof = roofline(dom, stage_ms[dom], spec, inf, peaks, src, len(F.chunks))
@@ -321,6 +325,7 @@ def run_ours(args):
         "mixed": mixed,
         "batch": batch,
         "screening": screening,
+        "coupled": coupled,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(spec, s, budget_s=args.cpu_budget)
@@ -444,6 +449,79 @@ def run_screening(args, dev, spec, s, coef, en, F):
             "pair_chi0_ms": t_pair, "screening_ms": t_scr,
             "screening_fp32_tflops": flops / (t_scr / 1e3) / 1e12,
             "newton_schulz_residual_max": float(res.max().item())}
+
+
+def run_coupled(args, dev, spec, W, om, F, peaks):
+    """The BSE with e-h / h-e coupling on the bench workload (A = F.H, P = F.P already built): coupling
+    pair densities and the coupling block B over the step's q chunks (FP32 and BF16x3 contractions), and
+    the coupled spectrum with 2 nsteps Lanczos steps (its zero-diagonal recursion needs twice the steps of
+    the Tamm-Dancoff one for the same resolution).  CUDA-event times; returns the JSON summary."""
+    import torch
+    from paper_1206_3518_gb300 import bse
+    from paper_1206_3518_gb300.pipeline import Coupled
+
+    plan = F.plan
+    inf = plan.info(0)
+    dim = inf["dim"]
+    nsteps = 2 * spec.nsteps
+    C = Coupled(F, nsteps=nsteps)
+    stream = torch.cuda.current_stream()
+
+    def build(prec, evs=None):
+        ev = (lambda: torch.cuda.Event(enable_timing=True)) if evs is not None else None
+        marks = []
+
+        def mark():
+            if ev:
+                e = ev()
+                e.record(stream)
+                marks.append(e)
+        mark()
+        bse.bse_build_coupling(plan, 0, bse.BSE_BC_INIT, F.rho_x, None, 0, 0, None, prec, C.Bm, C.ws)
+        mark()
+        for q0, q1 in F.chunks:
+            bse.bse_pair_densities(plan, 0, bse.BSE_PD_COUPLING, None, None, None, None, C.rho_cpl, q0, q1, F.ws_pair)
+            mark()
+            bse.bse_build_coupling(plan, 0, bse.BSE_BC_DIRECT, None, C.rho_cpl, q0, q1, W, prec, C.Bm, C.ws)
+            mark()
+        if evs is not None:
+            evs.append(marks)
+
+    out = {"workload": f"{spec.name}, dim {dim}, all {inf['nq']} q in {len(F.chunks)} chunks, {nsteps} coupled "
+                       f"Lanczos steps", "nsteps": nsteps}
+    res = {}
+    for name, prec in (("fp32", bse.BSE_PREC_FP32), ("bf16x3", bse.BSE_PREC_BF16X3)):
+        build(prec)
+        torch.cuda.synchronize()
+        bse.bse_status_read(plan)
+        evs = []
+        for _ in range(2):
+            build(prec, evs)
+        torch.cuda.synchronize()
+        bse.bse_status_read(plan)
+        init = statistics.mean(m[0].elapsed_time(m[1]) for m in evs)
+        pair = statistics.mean(sum(m[1 + 2 * i].elapsed_time(m[2 + 2 * i]) for i in range(len(F.chunks))) for m in evs)
+        contract = statistics.mean(sum(m[2 + 2 * i].elapsed_time(m[3 + 2 * i]) for i in range(len(F.chunks)))
+                                   for m in evs)
+        C.spectrum(om, spec.eta)
+        torch.cuda.synchronize()
+        bse.bse_status_read(plan)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        C.spectrum(om, spec.eta)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bse.bse_status_read(plan)
+        res[name] = C.eps2.clone()
+        out[name] = {"exchange_init_ms": init, "pair_coupling_ms": pair, "coupling_contract_ms": contract,
+                     "spectrum_ms": e0.elapsed_time(e1), "steps_done": int(C.steps_done.item())}
+    t = out["fp32"]["spectrum_ms"]
+    bytes_per_step = 2.0 * dim * dim * 8            # A and B, complex64, once per step
+    out["spectrum_hbm_gbs_equiv"] = nsteps * bytes_per_step / (t / 1e3) / 1e9
+    out["spectrum_hbm_frac_of_measured"] = out["spectrum_hbm_gbs_equiv"] / peaks["hbm_gbs"] if peaks else None
+    out["eps2_bf16x3_rel_err_vs_fp32"] = float((res["bf16x3"] - res["fp32"]).abs().max() / res["fp32"].abs().max())
+    out["coupled_spectra_per_s"] = 1e3 / t
+    return out
 
 
 def run_stage(args):
@@ -619,6 +697,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the BF16x3 comparison run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch of hexagonal sheets")
     ap.add_argument("--no-screening", action="store_true", help="skip the static RPA screening measurement")
+    ap.add_argument("--no-coupled", action="store_true", help="skip the BSE with e-h / h-e coupling")
     ap.add_argument("--only", default="all", choices=["all", "pair", "spectrum", "contract"],
                     help="profiling aid: run one stage (pair: realspace + a q chunk of pair densities; "
                          "spectrum: Haydock on an H built once before the loop)")

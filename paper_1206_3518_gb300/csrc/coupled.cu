@@ -22,13 +22,14 @@
 // One step j = one read of A and B:
 //   mv      t = A fl32(w_j) + sigma_j B conj(fl32(w_j)); partial sums of 2 Re(w_j^H t) per CTA
 //   update  beta_j^2 (each CTA sums the partials in the same order), breakdown test, b_j = beta_j,
-//           q_j = w_j / b_j, p_j = t / b_j, w_{j+1} = p_j - b_j q_{j-1}; projections of w_{j+1} on
-//           every p_i, i <= j, summed by the last CTA to finish
-//   reorth  w -= sum_i c_i q_i and the second projections; then w -= sum_i c'_i q_i and fl32(w)
-// No kernel waits for another CTA: cross-CTA sums use the last-block pattern (a counter whose last
-// arriving CTA reduces the partials), and the kernels of a step are ordered by the stream, so the whole
-// recursion is capturable in a CUDA graph.  q_j, w are FP64; the stored basis (q_i, p_i) and the
-// matrix-vector product are FP32.
+//           q_j = w_j / b_j, p_j = t / b_j, w_{j+1} = p_j - b_j q_{j-1}; partial projections of
+//           w_{j+1} on every p_i, i <= j, per CTA range
+//   reduce  the partials of all CTAs into <q_i, w>_M (one warp per i)
+//   reorth  w -= sum_i c_i q_i and the second partial projections; reduce; w -= sum_i c'_i q_i, fl32(w)
+// No kernel waits for another CTA: the kernels of a step are ordered by the stream, so the whole
+// recursion is capturable in a CUDA graph.  q_j, w, b_j and the cross-CTA sums are FP64; the stored basis
+// (q_i, p_i), the matrix-vector product and the per-CTA projection sums (corrections of rounding size)
+// are FP32.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -48,9 +49,9 @@ struct CplWs {
   float2* t;        // [dim] product of the current step
   float2* x32;      // [dim] fl32(w), the product's input
   double* mvpart;   // [kMaxMv] partial 2 Re(w^H t) per product CTA
-  double2* ppart;   // [kMaxVec][nsteps] partial p_i^H w per vector CTA
+  float2* ppart;    // [nsteps][kMaxVec] partial p_i^H w per vector CTA
   double2* c;       // [2][nsteps] M-inner products <q_i, w>_M of pass 1 and pass 2
-  int* ctl;         // [0] done, [1] steps, [2] [3] arrival counters of the two projection passes
+  int* ctl;         // [0] done, [1] steps
 };
 
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -66,7 +67,7 @@ CplWs carve(void* base, int dim, int nsteps) {
   w.t = (float2*)(p + o); o = al256(o + (size_t)dim * sizeof(float2));
   w.x32 = (float2*)(p + o); o = al256(o + (size_t)dim * sizeof(float2));
   w.mvpart = (double*)(p + o); o = al256(o + kMaxMv * sizeof(double));
-  w.ppart = (double2*)(p + o); o = al256(o + (size_t)kMaxVec * nsteps * sizeof(double2));
+  w.ppart = (float2*)(p + o); o = al256(o + (size_t)kMaxVec * nsteps * sizeof(float2));
   w.c = (double2*)(p + o); o = al256(o + 2 * (size_t)nsteps * sizeof(double2));
   w.ctl = (int*)(p + o); o = al256(o + 4 * sizeof(int));
   return w;
@@ -81,7 +82,7 @@ size_t carve_bytes(int dim, int nsteps) {
   o = al256(o + (size_t)dim * sizeof(float2));
   o = al256(o + (size_t)dim * sizeof(float2));
   o = al256(o + kMaxMv * sizeof(double));
-  o = al256(o + (size_t)kMaxVec * nsteps * sizeof(double2));
+  o = al256(o + (size_t)kMaxVec * nsteps * sizeof(float2));
   o = al256(o + 2 * (size_t)nsteps * sizeof(double2));
   o = al256(o + 4 * sizeof(int));
   return o;
@@ -125,8 +126,6 @@ __global__ void start_kernel(int dim, const double2* __restrict__ P, CplWs ws, d
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ws.ctl[0] = 0;
     ws.ctl[1] = nsteps;
-    ws.ctl[2] = 0;
-    ws.ctl[3] = 0;
   }
 }
 
@@ -212,53 +211,28 @@ __global__ __launch_bounds__(kMvThreads) void mv_kernel(int dim, const float2* _
   }
 }
 
-// Partial p_i^H w of this CTA's w (in s_w) for every i <= j; the last CTA to arrive sums the partials
-// of all CTAs (in CTA order), forms <q_i, w_{j+1}>_M (2 Re d for i of the parity of j+1, 2i Im d
-// otherwise) into cout[i] and rearms the counter.
-__device__ void project(const CplWs& ws, int dim, int j, int nsteps, int nset, int r0, int L,
-                        const double2* s_w, double2* __restrict__ cout, int* cnt) {
-  __shared__ int s_last;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int m = warp; m < nset; m += kVecWarps) {
-    const float2* Pi = ws.P32 + (size_t)m * dim + r0;
-    double ax = 0.0, ay = 0.0;
-    for (int i = lane; i < L; i += 32) {
-      const float2 pv = Pi[i];
-      const double2 wv = s_w[i];
-      ax += (double)pv.x * wv.x + (double)pv.y * wv.y;      // conj(p) w
-      ay += (double)pv.x * wv.y - (double)pv.y * wv.x;
+// Partial p_i^H w over this CTA's range for every i < nset (one thread per i, FP32 products and sums: the
+// coefficients are corrections of rounding size); ppart[i][cta].
+__device__ __forceinline__ void project_partials(const CplWs& ws, int dim, int nset, int r0, int L,
+                                                 const float2* s_wf) {
+  for (int i = threadIdx.x; i < nset; i += kVecThreads) {
+    const float2* Pi = ws.P32 + (size_t)i * dim + r0;
+    float ax = 0.f, ay = 0.f;
+#pragma unroll 8
+    for (int r = 0; r < L; ++r) {
+      const float2 pv = Pi[r], wv = s_wf[r];
+      ax = fmaf(pv.x, wv.x, fmaf(pv.y, wv.y, ax));      // conj(p) w
+      ay = fmaf(pv.x, wv.y, fmaf(-pv.y, wv.x, ay));
     }
-    ax = warp_sum(ax);
-    ay = warp_sum(ay);
-    if (lane == 0) ws.ppart[(size_t)blockIdx.x * nsteps + m] = make_double2(ax, ay);
+    ws.ppart[(size_t)i * kMaxVec + blockIdx.x] = make_float2(ax, ay);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = (atomicAdd(cnt, 1) == (int)gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  for (int m = warp; m < nset; m += kVecWarps) {
-    double ax = 0.0, ay = 0.0;
-    for (int c = lane; c < (int)gridDim.x; c += 32) {
-      const double2 v = __ldcg(ws.ppart + (size_t)c * nsteps + m);
-      ax += v.x;
-      ay += v.y;
-    }
-    ax = warp_sum(ax);
-    ay = warp_sum(ay);
-    if (lane == 0) cout[m] = (((m ^ (j + 1)) & 1) == 0) ? make_double2(2.0 * ax, 0.0) : make_double2(0.0, 2.0 * ay);
-  }
-  if (threadIdx.x == 0) *cnt = 0;
 }
 
 __global__ __launch_bounds__(kVecThreads) void update_kernel(int dim, int j, int nsteps, int nmv, CplWs ws,
                                                              double* __restrict__ b, int* __restrict__ status) {
   if (finished(ws)) return;
   __shared__ double s_beta2;
-  __shared__ double2 s_w[kMaxL];
+  __shared__ float2 s_wf[kMaxL];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
     double v = 0.0;
@@ -285,7 +259,6 @@ __global__ __launch_bounds__(kVecThreads) void update_kernel(int dim, int j, int
   range_of(dim, r0, r1);
   const int L = r1 - r0;
   const bool more = j + 1 < nsteps;
-  const int nset = more ? j + 1 : 0;
   double2* qcur = ws.qd + (size_t)(j & 1) * dim;
   const double2* qprev = ws.qd + (size_t)((j + 1) & 1) * dim;
   for (int i = threadIdx.x; i < L; i += kVecThreads) {
@@ -305,56 +278,77 @@ __global__ __launch_bounds__(kVecThreads) void update_kernel(int dim, int j, int
         wn.y -= bj * qp.y;
       }
       ws.w[r] = wn;
-      s_w[i] = wn;
-      if (nset == 0) ws.x32[r] = make_float2((float)wn.x, (float)wn.y);
+      s_wf[i] = make_float2((float)wn.x, (float)wn.y);
     }
   }
-  if (nset == 0) return;
+  if (!more) return;
   __syncthreads();
-  project(ws, dim, j, nsteps, nset, r0, L, s_w, ws.c, ws.ctl + 2);
+  project_partials(ws, dim, j + 1, r0, L, s_wf);
 }
 
-// w -= sum_{i <= j} <q_i, w>_M q_i (pass 1: then the second projections; pass 2: then fl32(w) for the product).
+// c[i] = <q_i, w_{j+1}>_M from the partials of all vector CTAs (one warp per i, FP64 sums in CTA order):
+// 2 Re d for i of the parity of j + 1, 2i Im d otherwise.
+__global__ __launch_bounds__(kVecThreads) void reduce_kernel(int j, int nvec_ctas, int pass, int nsteps, CplWs ws) {
+  if (finished(ws)) return;
+  const int i = blockIdx.x * kVecWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i > j) return;
+  double ax = 0.0, ay = 0.0;
+  for (int c = lane; c < nvec_ctas; c += 32) {
+    const float2 v = ws.ppart[(size_t)i * kMaxVec + c];
+    ax += (double)v.x;
+    ay += (double)v.y;
+  }
+  ax = warp_sum(ax);
+  ay = warp_sum(ay);
+  if (lane == 0)
+    ws.c[(size_t)(pass - 1) * nsteps + i] =
+        (((i ^ (j + 1)) & 1) == 0) ? make_double2(2.0 * ax, 0.0) : make_double2(0.0, 2.0 * ay);
+}
+
+// w -= sum_{i <= j} <q_i, w>_M q_i (pass 1: then the partials of the second projections; pass 2: then
+// fl32(w) for the product).  Threads take (element, group of i) so that many loads are in flight.
 __global__ __launch_bounds__(kVecThreads) void reorth_kernel(int dim, int j, int nsteps, int pass, CplWs ws) {
   if (finished(ws)) return;
-  __shared__ float2 part[kVecWarps][kMaxL];
-  __shared__ double2 s_w[kMaxL];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ float2 part[kVecThreads];
+  __shared__ float2 s_wf[kMaxL];
   const int nset = j + 1;
-  const double2* c = ws.c + (pass == 1 ? 0 : nsteps);
+  const double2* c = ws.c + (size_t)(pass - 1) * nsteps;
   int r0, r1;
   range_of(dim, r0, r1);
   const int L = r1 - r0;
-  for (int i = lane; i < L; i += 32) {
-    float2 acc = make_float2(0.f, 0.f);
+  const int ngrp = L > 0 ? (kVecThreads / L > 0 ? kVecThreads / L : 1) : 1;
+  const int t = threadIdx.x, rr = L > 0 ? t % L : 0, grp = L > 0 ? t / L : kVecThreads;
+  if (grp < ngrp) {
+    float ax = 0.f, ay = 0.f;
+    const float2* Qr = ws.Q32 + r0 + rr;
 #pragma unroll 4
-    for (int m = warp; m < nset; m += kVecWarps) {
-      const double2 cd = c[m];
+    for (int i = grp; i < nset; i += ngrp) {
+      const double2 cd = __ldg(c + i);
       const float cx = (float)cd.x, cy = (float)cd.y;
-      const float2 qv = ws.Q32[(size_t)m * dim + r0 + i];
-      acc.x = fmaf(cx, qv.x, fmaf(-cy, qv.y, acc.x));
-      acc.y = fmaf(cx, qv.y, fmaf(cy, qv.x, acc.y));
+      const float2 qv = Qr[(size_t)i * dim];
+      ax = fmaf(cx, qv.x, fmaf(-cy, qv.y, ax));
+      ay = fmaf(cx, qv.y, fmaf(cy, qv.x, ay));
     }
-    part[warp][i] = acc;
+    part[grp * L + rr] = make_float2(ax, ay);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < L; i += kVecThreads) {
-    float2 sum = part[0][i];
-#pragma unroll
-    for (int w = 1; w < kVecWarps; ++w) {
-      sum.x += part[w][i].x;
-      sum.y += part[w][i].y;
+  for (int i = t; i < L; i += kVecThreads) {
+    float sx = 0.f, sy = 0.f;
+    for (int g = 0; g < ngrp; ++g) {
+      sx += part[g * L + i].x;
+      sy += part[g * L + i].y;
     }
     double2 wv = ws.w[r0 + i];
-    wv.x -= (double)sum.x;
-    wv.y -= (double)sum.y;
+    wv.x -= (double)sx;
+    wv.y -= (double)sy;
     ws.w[r0 + i] = wv;
-    s_w[i] = wv;
-    if (pass == 2) ws.x32[r0 + i] = make_float2((float)wv.x, (float)wv.y);
+    const float2 wf = make_float2((float)wv.x, (float)wv.y);
+    s_wf[i] = wf;
+    if (pass == 2) ws.x32[r0 + i] = wf;
   }
   if (pass == 2) return;
   __syncthreads();
-  project(ws, dim, j, nsteps, nset, r0, L, s_w, ws.c + nsteps, ws.ctl + 3);
+  project_partials(ws, dim, nset, r0, L, s_wf);
 }
 
 __device__ __forceinline__ double2 cdivd(double2 a, double2 b) {
@@ -423,7 +417,10 @@ int launch_spectrum_coupled(const DevSys& d, const void* A, const void* Bm, cons
       mv_kernel<false><<<g1, kMvThreads, 0, st>>>(dim, (const float2*)A, (const float2*)Bm, sg, ws);
     update_kernel<<<g2, kVecThreads, 0, st>>>(dim, j, nsteps, g1, ws, b, status);
     if (j + 1 < nsteps) {
+      const int gr = (j + 1 + kVecWarps - 1) / kVecWarps;
+      reduce_kernel<<<gr, kVecThreads, 0, st>>>(j, g2, 1, nsteps, ws);
       reorth_kernel<<<g2, kVecThreads, 0, st>>>(dim, j, nsteps, 1, ws);
+      reduce_kernel<<<gr, kVecThreads, 0, st>>>(j, g2, 2, nsteps, ws);
       reorth_kernel<<<g2, kVecThreads, 0, st>>>(dim, j, nsteps, 2, ws);
     }
   }
