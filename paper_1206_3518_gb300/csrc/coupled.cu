@@ -396,7 +396,7 @@ int launch_spectrum_coupled(const DevSys& d, const void* A, const void* Bm, cons
   }
   const int dim = d.dim;
   if (dim > 65536) return -2;
-  int g1 = 2 * nsm;
+  int g1 = 3 * nsm;                      // three product CTAs per SM (the register limit)
   g1 = g1 > (dim + kMaxRows - 1) / kMaxRows ? g1 : (dim + kMaxRows - 1) / kMaxRows;
   g1 = g1 < (dim + 1) / 2 ? g1 : (dim + 1) / 2;
   g1 = g1 < kMaxMv ? g1 : kMaxMv;
