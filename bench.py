@@ -306,7 +306,7 @@ def run_ours(args):
 
     # dominant stage: by measured time
     dom = max(stage_ms, key=stage_ms.get)
-    roof = roofline(dom, stage_ms[dom], spec, inf, peaks, src, len(F.chunks))
+    roof = roofline(dom, stage_ms[dom], spec, inf, peaks, src, len(F.chunks), pair_work(plan, spec, inf))
     out = {
         "metric": METRIC, "value": world * dim * dim / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -595,7 +595,17 @@ def run_stage(args):
 # DRAM bytes (read + write) of one full-size pair_kernel launch of the fcc 8x8x8 3v4c workload from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass), valid while the kernel
 # sources hash to the recorded value; see profiles/launches_fcc8x8x8_3v4c_fp32.md.
+# DRAM bytes (read + write) of one full-size correlation-kernel launch (direct set, all 512 q), from one ncu
+# capture of the sources with this SHA-1 (gcorr.cu + pairjob.cuh); not reported for other sources.
+GCORR_TRAFFIC = {"sha1": None, "bytes": None}
 PAIR_TRAFFIC = {"sha1": "c39047a0b9675fda883a64bbde1871fdae56455a", "bytes": 101.77e9 + 8.39e9}
+
+
+def _gcorr_sources_sha1():
+    import hashlib
+    base = os.path.join(ROOT, "paper_1206_3518_gb300", "csrc")
+    data = open(os.path.join(base, "gcorr.cu"), "rb").read() + open(os.path.join(base, "pairjob.cuh"), "rb").read()
+    return hashlib.sha1(data).hexdigest()
 
 
 def _pair_sources_sha1():
@@ -605,11 +615,39 @@ def _pair_sources_sha1():
     return hashlib.sha1(data).hexdigest()
 
 
-def roofline(stage, ms, spec, inf, peaks, src, nchunks):
+def pair_work(plan, spec, inf):
+    """Variant in use for the direct pair densities and, for the plane-wave correlation kernel, its complex
+    multiply-adds over all upper blocks: sum_blocks NG(q) |S(k')| (Nv^2 + Nc^2) (the dense (p, G2) loop)."""
+    from paper_1206_3518_gb300 import bse
+    variants, current = bse.bse_pair_variants(plan, 0)
+    v = next(x for x in variants if x["index"] == current)
+    if v["rows"] != 0:
+        return {"method": "fft", "variant": current}
+    npw = [len(bse.bse_gvectors(plan, 0, k, 0)) for k in range(spec.nkpt)]
+    cmac = 0
+    for q in range(spec.nkpt):
+        ng = len(bse.bse_gvectors(plan, 0, q, 1))
+        blk, _ = bse.bse_pair_blocks(plan, 0, q)
+        cmac += ng * sum(npw[int(k2)] for _, k2 in blk)
+    return {"method": "correlation", "variant": current, "cmac": cmac * (spec.nv ** 2 + spec.nc ** 2)}
+
+
+def roofline(stage, ms, spec, inf, peaks, src, nchunks, pw=None):
     """Algorithmic work of the dominant stage per launch over its measured mean duration."""
     dim = inf["dim"]
     nb = inf["nblocks"]
     n1, n2, n3 = spec.fft
+    if stage == "pair_direct" and pw and pw["method"] == "correlation":
+        flops = 8.0 * pw["cmac"] / nchunks
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = flops / (ms / 1e3) / 1e12
+        return {"bound": "alu", "kernel": "gcorr_kernel", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak,
+                "work": "8 FP32 flops per complex multiply-add of the plane-wave correlation's (G, G2) loop: "
+                        "sum over blocks of NG(q) |S(k')| (Nv^2 + Nc^2)",
+                "traffic": (GCORR_TRAFFIC["bytes"] if nchunks == 1 and spec.name == "fcc_8x8x8_3v4c"
+                            and _gcorr_sources_sha1() == GCORR_TRAFFIC["sha1"] else None),
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"}
     if stage == "pair_direct":
         import math
         nr = n1 * n2 * n3

@@ -1,0 +1,259 @@
+// Pair densities by direct plane-wave correlation (step A2; Eq. pair_density in the plane-wave basis).
+//
+//   rho_nm^{kk'}(G) = sum_{G2 in S(k')} conj(c_nk(G2 - G)) c_mk'(G2),   G = g_p(q) - G0,
+//
+// c_nk(G1) = 0 outside the sphere S(k).  This is the same quantity as the pruned-FFT route of
+// pair.cu (the FFT of conj(u_nk) u_mk' evaluated on the sphere of q), computed without the real-space
+// grid: on these workloads a sphere holds ~1% of the FFT box (fcc 8x8x8: ~300 of 32^3 points), so
+// the correlation takes ~4x fewer multiply-adds per band product than the FFT kernel spends, needs no
+// grid, and has no aliasing condition.
+//
+// One CTA per job (decode_job of pairjob.cuh: the blocks of the direct and coupling sets, the
+// exchange set, or the (k, k+q) set of the screening), one thread per sphere point p of q.
+// Shared memory holds the job's coefficients at k (planar per band, plus a zero row), those at k'
+// (packed per G2 for broadcast loads), and a dense index box of S(k) over the key range
+// G2 - G (per axis |.| <= fwf + fpair), whose entries outside the sphere point at the zero row.  The
+// inner loop runs over G2: one box lookup, a
+// gather of the k bands and a broadcast of the k' bands, then every band product of the job as FP32
+// complex multiply-adds; iterations in which no lane of a warp has a partner in S(k) are skipped.  The
+// G = 0 overlaps of the diagonal blocks are summed again in FP64.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "pairjob.cuh"
+
+namespace bse {
+namespace {
+
+using namespace pj;
+
+constexpr int kGcMaxThreads = 576;      // one thread per sphere point up to 576 points (fcc 12x12x12: 531); 113 registers
+
+// KIND 0: v x c at (k, k') (exchange and screening sets), 1: vv' then cc' (direct set),
+// 2: vc' then cv' (coupling set).
+template <int NV, int NC, int KIND>
+struct Shape {
+  static constexpr int NB = NV + NC;
+  static constexpr int NA = KIND == 0 ? NV : NB;      // bands at k
+  static constexpr int NK = KIND == 0 ? NC : NB;      // bands at k'
+  static constexpr int NKP = (NK + 1) & ~1;           // packed row of k' bands (float4 loads)
+  static constexpr int P = KIND == 0 ? NV * NC : (KIND == 1 ? NV * NV + NC * NC : 2 * NV * NC);
+  // band at k, band at k', output (0: out_v, 1: out_c), index within that output
+  static constexpr int a(int p) {
+    return KIND == 0 ? p / NC : KIND == 1 ? (p < NV * NV ? p / NV : NV + (p - NV * NV) / NC)
+                                          : (p < NV * NC ? p / NC : NV + (p - NV * NC) / NV);
+  }
+  static constexpr int b(int p) {
+    return KIND == 0 ? p % NC : KIND == 1 ? (p < NV * NV ? p % NV : NV + (p - NV * NV) % NC)
+                                          : (p < NV * NC ? NV + p % NC : (p - NV * NC) % NV);
+  }
+  static constexpr int o(int p) { return KIND == 0 ? 0 : KIND == 1 ? (p < NV * NV ? 0 : 1) : (p < NV * NC ? 0 : 1); }
+  static constexpr int t(int p) {
+    return KIND == 0 ? p : KIND == 1 ? (p < NV * NV ? p : p - NV * NV) : (p < NV * NC ? p : p - NV * NC);
+  }
+};
+
+struct Box {
+  int rx, ry, rz, dy, dz, n;   // key (g1, g2, g3) -> ((g1 + rx) dy + g2 + ry) dz + g3 + rz
+};
+
+template <int NV, int NC, int KIND>
+size_t smem_bytes(const DevSys& d, const Box& bx) {
+  using S = Shape<NV, NC, KIND>;
+  const size_t ca = (size_t)S::NA * (d.npw_max + 1) * sizeof(float2);
+  const size_t cb = (size_t)d.npw_max * S::NKP * sizeof(float2);
+  const size_t lin = (size_t)d.npw_max * sizeof(int);
+  const size_t box = ((size_t)bx.n * sizeof(unsigned short) + 15) & ~(size_t)15;
+  return ((ca + 15) & ~(size_t)15) + cb + lin + box;
+}
+
+// Diagonal blocks (k = k', q = 0, G0 = 0): the first sphere point is G = 0, where the overlaps
+// rho_nm^{kk}(0) are delta_nm (0 for the coupling set) up to rounding and meet the q = 0 head of W
+// (~1e4 Ha bohr^3 for the slab workloads).  One warp sums them again with FP64 accumulation.
+template <int NV, int NC, int KIND>
+__device__ __noinline__ void g0_overlaps(const float2* ca, const float2* cb2, int stride, int n2, const Job& jb,
+                                         int ng_max) {
+  using S = Shape<NV, NC, KIND>;
+  const int lane = threadIdx.x & 31;
+  for (int q = 0; q < S::P; ++q) {
+    double sr = 0.0, si = 0.0;
+    for (int i = lane; i < n2; i += 32) {
+      const float2 x = ca[S::a(q) * stride + i], y = cb2[i * S::NKP + S::b(q)];
+      sr += (double)x.x * y.x + (double)x.y * y.y;        // conj(x) y
+      si += (double)x.x * y.y - (double)x.y * y.x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) {
+      float2* dst = (S::o(q) == 0 ? jb.out_v : jb.out_c) + (size_t)S::t(q) * ng_max;
+      dst[0] = make_float2((float)sr, (float)si);
+    }
+  }
+}
+
+template <int NV, int NC, int KIND>
+__global__ __launch_bounds__(kGcMaxThreads) void gcorr_kernel(DevSys d, const float2* __restrict__ coef,
+                                                              float2* __restrict__ out, int mode, int q0, int nqc,
+                                                              long long vbase, Box bx) {
+  using S = Shape<NV, NC, KIND>;
+  constexpr int NA = S::NA, NK = S::NK, NKP = S::NKP, P = S::P;
+  Job jb;
+  if (!decode_job(d, mode, true, q0, nqc, vbase, out, jb)) return;
+  extern __shared__ __align__(16) float4 smv[];
+  const int stride = d.npw_max + 1;                    // planar k rows; index npw_max is the zero row
+  float2* ca = reinterpret_cast<float2*>(smv);
+  const size_t ca_bytes = (((size_t)NA * stride * sizeof(float2)) + 15) & ~(size_t)15;
+  float4* cb = reinterpret_cast<float4*>(reinterpret_cast<char*>(smv) + ca_bytes);   // [npw_max][NKP/2]
+  int* lin2 = reinterpret_cast<int*>(cb + (size_t)d.npw_max * (NKP / 2));
+  unsigned short* box = reinterpret_cast<unsigned short*>(lin2 + d.npw_max);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int zrow = d.npw_max;
+  const int n1 = d.npw[jb.k], n2 = d.npw[jb.k2];
+
+  for (int i = tid; i < bx.n; i += nt) box[i] = (unsigned short)zrow;
+  for (int i = tid; i < NA * stride; i += nt) {
+    const int n = i / stride, g = i - n * stride;
+    ca[i] = g < n1 ? coef[((size_t)jb.k * d.nb + jb.a0 + n) * d.npw_max + g] : make_float2(0.f, 0.f);
+  }
+  float2* cb2 = reinterpret_cast<float2*>(cb);
+  for (int i = tid; i < n2 * NKP; i += nt) {
+    const int g = i / NKP, m = i - g * NKP;
+    cb2[i] = m < NK ? coef[((size_t)jb.k2 * d.nb + jb.b0 + m) * d.npw_max + g] : make_float2(0.f, 0.f);
+  }
+  for (int i = tid; i < n2; i += nt) {
+    const char4 g = d.gk[(size_t)jb.k2 * d.npw_max + i];
+    lin2[i] = ((int)g.x * bx.dy + (int)g.y) * bx.dz + (int)g.z;
+  }
+  __syncthreads();
+  for (int i = tid; i < n1; i += nt) {
+    const char4 g = d.gk[(size_t)jb.k * d.npw_max + i];
+    box[(((int)g.x + bx.rx) * bx.dy + (int)g.y + bx.ry) * bx.dz + (int)g.z + bx.rz] = (unsigned short)i;
+  }
+  __syncthreads();
+
+  const int NG = d.ngq[jb.q];
+  for (int p0 = 0; p0 < NG; p0 += nt) {
+    const int p = p0 + tid;
+    const bool act = p < NG;
+    const char4 gp = d.gq[(size_t)jb.q * d.ng_max + (act ? p : 0)];
+    // key of G1 = G2 - G with G = g_p - G0
+    const int base = ((-(int)gp.x + jb.g0x + bx.rx) * bx.dy + (-(int)gp.y + jb.g0y + bx.ry)) * bx.dz +
+                     (-(int)gp.z + jb.g0z + bx.rz);
+    float acc[2 * P];
+#pragma unroll
+    for (int i = 0; i < 2 * P; ++i) acc[i] = 0.f;
+    for (int i = 0; i < n2; ++i) {
+      const int idx = box[base + lin2[i]];
+      if (__all_sync(0xffffffffu, idx == zrow)) continue;     // no lane of this warp has G2 - G in S(k)
+      float2 a[NA];
+#pragma unroll
+      for (int n = 0; n < NA; ++n) a[n] = ca[n * stride + idx];
+      float2 bv[NKP];
+#pragma unroll
+      for (int m = 0; m < NKP / 2; ++m) {
+        const float4 v = cb[(size_t)i * (NKP / 2) + m];
+        bv[2 * m] = make_float2(v.x, v.y);
+        bv[2 * m + 1] = make_float2(v.z, v.w);
+      }
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const float2 x = a[S::a(q)], y = bv[S::b(q)];
+        acc[2 * q] = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[2 * q]));          // conj(x) y
+        acc[2 * q + 1] = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc[2 * q + 1]));
+      }
+    }
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        float2* dst = (S::o(q) == 0 ? jb.out_v : jb.out_c) + (size_t)S::t(q) * d.ng_max;
+        dst[p] = make_float2(acc[2 * q], acc[2 * q + 1]);
+      }
+    }
+    if (KIND != 0 && p0 == 0 && tid < 32 && jb.k == jb.k2) {
+      const char4 g = d.gq[(size_t)jb.q * d.ng_max];
+      if (g.x == 0 && g.y == 0 && g.z == 0 && jb.g0x == 0 && jb.g0y == 0 && jb.g0z == 0) {
+        __syncwarp();
+        g0_overlaps<NV, NC, KIND>(ca, cb2, stride, n2, jb, d.ng_max);
+      }
+    }
+  }
+}
+
+typedef void (*GcFn)(DevSys, const float2*, float2*, int, int, int, long long, Box);
+
+struct GcEntry {
+  int nv, nc;
+  GcFn fn[3];
+  size_t (*smem[3])(const DevSys&, const Box&);
+};
+
+#define BSE_GC(NV, NC)                                                                                   \
+  GcEntry {                                                                                              \
+    NV, NC, {gcorr_kernel<NV, NC, 0>, gcorr_kernel<NV, NC, 1>, gcorr_kernel<NV, NC, 2>}, {                \
+      smem_bytes<NV, NC, 0>, smem_bytes<NV, NC, 1>, smem_bytes<NV, NC, 2>                                 \
+    }                                                                                                    \
+  }
+
+// band counts compiled: the fcc workloads (3v3c, 3v4c, 4v4c, the 2v2c test cell) and every
+// hexagonal sheet of the batch (1-3 valence x 1-3 conduction)
+const GcEntry kGc[] = {
+    BSE_GC(3, 4), BSE_GC(3, 3), BSE_GC(4, 4), BSE_GC(2, 2), BSE_GC(1, 1), BSE_GC(1, 2),
+    BSE_GC(1, 3), BSE_GC(2, 1), BSE_GC(2, 3), BSE_GC(3, 1), BSE_GC(3, 2),
+};
+
+const GcEntry* find(const DevSys& d) {
+  for (const GcEntry& e : kGc)
+    if (e.nv == d.nv && e.nc == d.nc) return &e;
+  return nullptr;
+}
+
+Box box_of(const DevSys& d) {
+  Box b;
+  b.rx = d.fwf[0] + d.fpair[0];
+  b.ry = d.fwf[1] + d.fpair[1];
+  b.rz = d.fwf[2] + d.fpair[2];
+  b.dy = 2 * b.ry + 1;
+  b.dz = 2 * b.rz + 1;
+  b.n = (2 * b.rx + 1) * b.dy * b.dz;
+  return b;
+}
+
+int threads_of(const DevSys& d) {
+  int t = (d.ng_max + 31) / 32 * 32;
+  return t < kGcMaxThreads ? t : kGcMaxThreads;
+}
+
+}  // namespace
+
+// Valid when the band counts are compiled, the sphere index fits 16 bits and shared memory suffices.
+int gcorr_valid(const DevSys& d) {
+  const GcEntry* e = find(d);
+  if (!e || d.npw_max >= 65535) return 0;
+  const Box bx = box_of(d);
+  for (int k = 0; k < 3; ++k)
+    if (e->smem[k](d, bx) > 227 * 1024) return 0;
+  return 1;
+}
+
+int gcorr_threads(const DevSys& d) { return threads_of(d); }
+
+// kind 0: exchange / screening sets, 1: direct set, 2: coupling set; cells = CTAs of the launch.
+int launch_gcorr(const DevSys& d, const void* coef, void* out, int kind, int mode, int q0, int nqc, long long vbase,
+                 long long cells, void* stream) {
+  const GcEntry* e = find(d);
+  if (!e || kind < 0 || kind > 2) return (int)cudaErrorInvalidValue;
+  if (cells <= 0) return 0;
+  if (cells >= (1LL << 31)) return (int)cudaErrorInvalidValue;
+  const Box bx = box_of(d);
+  const size_t sm = e->smem[kind](d, bx);
+  int err = (int)cudaFuncSetAttribute((const void*)e->fn[kind], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (err) return err;
+  e->fn[kind]<<<(unsigned)cells, threads_of(d), sm, (cudaStream_t)stream>>>(d, (const float2*)coef, (float2*)out,
+                                                                          mode, q0, nqc, vbase, bx);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace bse

@@ -29,6 +29,7 @@
 #include <cmath>
 
 #include "fft.cuh"
+#include "pairjob.cuh"
 #include "internal.h"
 
 namespace bse {
@@ -136,178 +137,7 @@ struct PairCfg {
   }
 };
 
-// Jobs are laid out over the (q, k) cells of a q chunk in tiles of kTQ x kTK so that
-// CTAs running together share wavefunction slabs in L2.
-constexpr int kTQ = 8, kTK = 16;
-
-struct Job {
-  int k, k2, a0, na, b0, nb, q, g0x, g0y, g0z;
-  int mode;             // 0 (v x c) products, 1 vv', 2 cc', 3 vv' then cc';
-                        // coupling: 5 vc' then cv', 6 vc', 7 cv'
-  float2* out_v;        // first output vector of the vv' (exchange, vc') products
-  float2* out_c;        // first output vector of the cc' (cv') products
-};
-
-__device__ __forceinline__ int nprod(const DevSys& d, int mode) {
-  switch (mode) {
-    case 0: case 6: case 7: return d.nv * d.nc;
-    case 1: return d.nv * d.nv;
-    case 2: return d.nc * d.nc;
-    case 5: return 2 * d.nv * d.nc;
-    default: return d.nv * d.nv + d.nc * d.nc;
-  }
-}
-
-__device__ __forceinline__ bool decode_job(const DevSys& d, int mode, bool merged, int q0, int nqc, long long vbase,
-                                           float2* out, Job& j) {
-  if (mode == 4) {                         // v at k, c at k' = fold(k + q), k + q = k' + G0 (all k)
-    const int qi = (int)(blockIdx.x / d.nkpt), k = (int)(blockIdx.x - (long long)qi * d.nkpt);
-    const int q = q0 + qi;
-    const int k1 = k / (d.nk2 * d.nk3), k2 = (k / d.nk3) % d.nk2, k3 = k % d.nk3;
-    const int q1 = q / (d.nk2 * d.nk3), q2 = (q / d.nk3) % d.nk2, q3 = q % d.nk3;
-    const int s1 = k1 + q1, s2 = k2 + q2, s3 = k3 + q3;
-    const int f1 = s1 % d.nk1, f2 = s2 % d.nk2, f3 = s3 % d.nk3;
-    j.k = k;
-    j.k2 = (f1 * d.nk2 + f2) * d.nk3 + f3;
-    j.q = q;
-    j.g0x = -(s1 / d.nk1);                 // sampled at G - g0 = G + G0
-    j.g0y = -(s2 / d.nk2);
-    j.g0z = -(s3 / d.nk3);
-    j.a0 = 0;
-    j.na = d.nv;
-    j.b0 = d.nv;
-    j.nb = d.nc;
-    j.mode = 0;
-    j.out_v = out + ((size_t)qi * d.nkpt + k) * d.nv * d.nc * d.ng_max;
-    j.out_c = nullptr;
-    return true;
-  }
-  if (mode == 0) {
-    j.k = j.k2 = blockIdx.x;
-    j.a0 = 0;
-    j.na = d.nv;
-    j.b0 = d.nv;
-    j.nb = d.nc;
-    j.q = 0;
-    j.g0x = j.g0y = j.g0z = 0;
-    j.mode = 0;
-    j.out_v = out + (size_t)blockIdx.x * d.nv * d.nc * d.ng_max;
-    j.out_c = nullptr;
-    return true;
-  }
-  long long cell = blockIdx.x;
-  int group = 0;
-  if (!merged) {
-    group = (int)(cell & 1);
-    cell >>= 1;
-  }
-  const int ntk = (d.nkpt + kTK - 1) / kTK;
-  const long long tile = cell / (kTQ * kTK);
-  const int u = (int)(cell - tile * (kTQ * kTK));
-  const int tq = (int)(tile / ntk), tk = (int)(tile - (long long)tq * ntk);
-  const int q = q0 + tq * kTQ + u / kTK;
-  const int k = tk * kTK + u % kTK;
-  if (q >= q0 + nqc || k >= d.nkpt) return false;
-  const int b = d.blkidx[(size_t)q * d.nkpt + k];
-  if (b < 0) return false;
-  const int4 blk = d.blocks[b];
-  j.k = blk.x;
-  j.k2 = blk.y;
-  j.q = blk.z;
-  j.g0x = (blk.w & 3) - 1;
-  j.g0y = ((blk.w >> 2) & 3) - 1;
-  j.g0z = ((blk.w >> 4) & 3) - 1;
-  const long long qb = d.qblk_off[q];
-  const long long nblk = d.qblk_off[q + 1] - qb;
-  const long long local = b - qb;
-  if (mode == 5) {                         // coupling densities: per q [nblk][Nv Nc] vc', then [nblk][Nc Nv] cv'
-    const long long w = (long long)d.nv * d.nc;
-    const long long cbase = 2 * w * qb - vbase;
-    j.out_v = out + (size_t)(cbase + local * w) * d.ng_max;
-    j.out_c = out + (size_t)(cbase + nblk * w + local * w) * d.ng_max;
-    if (merged) {
-      j.mode = 5;
-      j.a0 = j.b0 = 0;
-      j.na = j.nb = d.nb;
-    } else if (group == 0) {               // v at k, c at k'
-      j.mode = 6;
-      j.a0 = 0;
-      j.na = d.nv;
-      j.b0 = d.nv;
-      j.nb = d.nc;
-    } else {                               // c at k, v at k'
-      j.mode = 7;
-      j.a0 = d.nv;
-      j.na = d.nc;
-      j.b0 = 0;
-      j.nb = d.nv;
-    }
-    return true;
-  }
-  const long long base = d.qvec_off[q] - vbase;
-  j.out_v = out + (size_t)(base + local * d.nv * d.nv) * d.ng_max;
-  j.out_c = out + (size_t)(base + nblk * d.nv * d.nv + local * d.nc * d.nc) * d.ng_max;
-  if (merged) {
-    j.mode = 3;
-    j.a0 = j.b0 = 0;
-    j.na = j.nb = d.nb;
-  } else if (group == 0) {
-    j.mode = 1;
-    j.a0 = j.b0 = 0;
-    j.na = j.nb = d.nv;
-  } else {
-    j.mode = 2;
-    j.a0 = j.b0 = d.nv;
-    j.na = j.nb = d.nc;
-  }
-  return true;
-}
-
-// product p -> (slab of the n band, slab of the m band, output vector)
-__device__ __forceinline__ void product_of(const DevSys& d, const Job& j, int p, int& sa, int& sb, float2*& dst) {
-  const int nv = d.nv, nc = d.nc;
-  if (j.mode == 0) {                       // (v, c) at k = k'
-    sa = p / nc;
-    sb = j.na + p % nc;
-    dst = j.out_v + (size_t)p * d.ng_max;
-  } else if (j.mode == 1) {                // (v, v')
-    sa = p / nv;
-    sb = j.na + p % nv;
-    dst = j.out_v + (size_t)p * d.ng_max;
-  } else if (j.mode == 2) {                // (c, c')
-    sa = p / nc;
-    sb = j.na + p % nc;
-    dst = j.out_c + (size_t)p * d.ng_max;
-  } else if (j.mode == 5) {                // merged coupling: (v, c') then (c, v'); slabs hold all nb bands
-    if (p < nv * nc) {
-      sa = p / nc;
-      sb = j.na + nv + p % nc;
-      dst = j.out_v + (size_t)p * d.ng_max;
-    } else {
-      const int t = p - nv * nc;
-      sa = nv + t / nv;
-      sb = j.na + t % nv;
-      dst = j.out_c + (size_t)t * d.ng_max;
-    }
-  } else if (j.mode == 6) {                // (v at k, c' at k')
-    sa = p / nc;
-    sb = j.na + p % nc;
-    dst = j.out_v + (size_t)p * d.ng_max;
-  } else if (j.mode == 7) {                // (c at k, v' at k')
-    sa = p / nv;
-    sb = j.na + p % nv;
-    dst = j.out_c + (size_t)p * d.ng_max;
-  } else if (p < nv * nv) {                // merged: (v, v') then (c, c'); slabs hold all nb bands
-    sa = p / nv;
-    sb = j.na + p % nv;
-    dst = j.out_v + (size_t)p * d.ng_max;
-  } else {
-    const int t = p - nv * nv;
-    sa = nv + t / nc;
-    sb = j.na + nv + t % nc;
-    dst = j.out_c + (size_t)t * d.ng_max;
-  }
-}
+using namespace pj;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -589,6 +419,7 @@ bool valid_for(const Variant& v, const DevSys& d) {
   return ok && pm <= v.pmax && bd <= v.bmax && d.nb <= v.bmax && d.ng_max <= v.ppt * v.threads;
 }
 
+// FFT variant for the real-space stage and for pair launches when no correlation variant is in use.
 const Variant* pick(const DevSys& d) {
   if (d.pair_variant >= 0 && d.pair_variant < kNumVariants && valid_for(kVariants[d.pair_variant], d))
     return &kVariants[d.pair_variant];
@@ -596,6 +427,18 @@ const Variant* pick(const DevSys& d) {
     if (valid_for(v, d)) return &v;
   return nullptr;
 }
+
+// The plane-wave correlation kernel (gcorr.cu) is variant kGcorrIndex; it is the default wherever it
+// is compiled for the system's band counts, and the FFT variants stay selectable.
+constexpr int kGcorrIndex = 64;
+bool use_gcorr(const DevSys& d) {
+  if (!gcorr_valid(d)) return false;
+  return d.pair_variant == -1 || d.pair_variant == kGcorrIndex;
+}
+
+// Coefficients c_nk(G) are kept after u_nk(r) in the pair workspace (the correlation kernel reads them).
+size_t u_bytes(const DevSys& d) { return ((size_t)d.nkpt * d.nb * d.n1 * d.n2 * d.n3 * 8 + 255) & ~(size_t)255; }
+const void* coef_copy(const DevSys& d, const void* ws) { return (const char*)ws + u_bytes(d); }
 
 // Tensor map of the u(r) workspace as a 2D array of z-lines ([Nk Nb N1 N2] lines x N3 complex,
 // 8-byte elements); boxes of (N3 + 2) x ROWS, out-of-bounds elements read as zero.
@@ -628,8 +471,23 @@ int upload_twiddles() {
 
 int pair_supported(const DevSys& d) { return pick(d) != nullptr; }
 
+size_t pair_ws_bytes(const DevSys& d) { return u_bytes(d) + (size_t)d.nkpt * d.nb * d.npw_max * 8; }
+
 int pair_variants(const DevSys& d, int* out, int cap) {
   int n = 0;
+  if (gcorr_valid(d)) {                      // rows = 0 marks the plane-wave correlation kernel
+    if (out && n < cap) {
+      int* o = out + 7 * n;
+      o[0] = kGcorrIndex;
+      o[1] = gcorr_threads(d);
+      o[2] = 0;
+      o[3] = 2 * d.nv * d.nc > d.nv * d.nv + d.nc * d.nc ? 2 * d.nv * d.nc : d.nv * d.nv + d.nc * d.nc;
+      o[4] = 2 * d.nb;
+      o[5] = 1;
+      o[6] = 1;
+    }
+    ++n;
+  }
   for (int i = 0; i < kNumVariants; ++i) {
     const Variant& v = kVariants[i];
     if (!valid_for(v, d)) continue;
@@ -649,6 +507,7 @@ int pair_variants(const DevSys& d, int* out, int cap) {
 }
 
 int pair_variant_current(const DevSys& d) {
+  if (use_gcorr(d)) return kGcorrIndex;
   const Variant* v = pick(d);
   return v ? (int)(v - kVariants) : -1;
 }
@@ -658,10 +517,13 @@ int launch_realspace(const DevSys& d, const void* coef, void* u, void* stream) {
   if (!v) return (int)cudaErrorInvalidValue;
   cudaFuncSetAttribute((const void*)v->rs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->rs_smem);
   v->rs<<<d.nkpt * d.nb, kThreads, v->rs_smem, (cudaStream_t)stream>>>(d, (const float2*)coef, (float2*)u);
-  return (int)cudaGetLastError();
+  if (int e = (int)cudaGetLastError()) return e;
+  return (int)cudaMemcpyAsync((char*)u + u_bytes(d), coef, (size_t)d.nkpt * d.nb * d.npw_max * 8,
+                              cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
 }
 
 int launch_pair_exchange(const DevSys& d, const void* u, void* rho_x, int* status, void* stream) {
+  if (use_gcorr(d)) return launch_gcorr(d, coef_copy(d, u), rho_x, 0, 0, 0, 0, 0, d.nkpt, stream);
   const Variant* v = pick(d);
   if (!v) return (int)cudaErrorInvalidValue;
   const size_t sm = v->pair_smem(d.ng_max);
@@ -672,8 +534,16 @@ int launch_pair_exchange(const DevSys& d, const void* u, void* rho_x, int* statu
   return (int)cudaGetLastError();
 }
 
+static long long job_cells(const DevSys& d, int nqc, bool merged) {
+  const long long ntk = (d.nkpt + kTK - 1) / kTK, ntq = (nqc + kTQ - 1) / kTQ;
+  return ntq * ntk * kTQ * kTK * (merged ? 1 : 2);
+}
+
 int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, int q_begin, int q_end, long long vbase,
                        int* status, void* stream) {
+  if (use_gcorr(d))
+    return launch_gcorr(d, coef_copy(d, u), rho_dir, 1, 1, q_begin, q_end - q_begin, vbase,
+                        job_cells(d, q_end - q_begin, true), stream);
   const Variant* v = pick(d);
   if (!v) return (int)cudaErrorInvalidValue;
   const size_t sm = v->pair_smem(d.ng_max);
@@ -693,6 +563,9 @@ int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, int q_begi
 // job tiling as the direct set; nv^2 + nc^2 >= 2 nv nc, so every variant valid there fits these).
 int launch_pair_coupling(const DevSys& d, const void* u, void* rho_cpl, int q_begin, int q_end, long long vbase,
                          int* status, void* stream) {
+  if (use_gcorr(d))
+    return launch_gcorr(d, coef_copy(d, u), rho_cpl, 2, 5, q_begin, q_end - q_begin, vbase,
+                        job_cells(d, q_end - q_begin, true), stream);
   const Variant* v = pick(d);
   if (!v) return (int)cudaErrorInvalidValue;
   const size_t sm = v->pair_smem(d.ng_max);
@@ -710,6 +583,9 @@ int launch_pair_coupling(const DevSys& d, const void* u, void* rho_cpl, int q_be
 
 // rho_vc^{k,k+q}(G) for every k and q in [q_begin, q_end): rows ((q - q_begin) Nk + k) Nv Nc + v Nc + c.
 int launch_pair_chi0(const DevSys& d, const void* u, void* rho, int q_begin, int q_end, int* status, void* stream) {
+  if (use_gcorr(d))
+    return launch_gcorr(d, coef_copy(d, u), rho, 0, 4, q_begin, q_end - q_begin, 0,
+                        (long long)(q_end - q_begin) * d.nkpt, stream);
   const Variant* v = pick(d);
   if (!v) return (int)cudaErrorInvalidValue;
   const size_t sm = v->pair_smem(d.ng_max);

@@ -439,7 +439,7 @@ bse_status bse_workspace_size(const bse_plan* plan, int s, int kind, long long a
   const DevSys& d = plan->sys[s].d;
   switch (kind) {
     case BSE_WS_PAIR:
-      *bytes = (size_t)d.nkpt * d.nb * d.n1 * d.n2 * d.n3 * 8;
+      *bytes = pair_ws_bytes(d);
       return BSE_OK;
     case BSE_WS_KERNEL:
       if (arg < 1 || arg > d.nq) return set_error(BSE_ERR_ARG, "q chunk out of range");
@@ -547,7 +547,7 @@ bse_status bse_set_pair_variant(bse_plan* plan, int s, int index) {
   if (st != BSE_OK) return st;
   DevSys& d = plan->sys[s].d;
   if (index != -1) {
-    int buf[7 * 64];
+    int buf[7 * 65];
     const int n = pair_variants(d, buf, 64);
     bool found = false;
     for (int i = 0; i < n && i < 64; ++i) found = found || buf[7 * i] == index;

@@ -1,8 +1,9 @@
-"""Pair-kernel tile-shape variants and their autotuner (through the C ABI).
+"""Pair-kernel variants and their autotuner (through the C ABI).
 
-The variants only re-partition the same arithmetic (per z-line FFTs, per-slab y FFTs, the x DFT
-accumulated slab by slab in the same order), so every variant must give bit-identical pair
-densities; one of them is also compared with the oracle's plane-wave correlation.
+The pruned-FFT variants only re-partition the same arithmetic (per z-line FFTs, per-slab y FFTs, the
+x DFT accumulated slab by slab in the same order), so they must give bit-identical pair densities.
+The plane-wave correlation variant (rows = 0, the default where it is compiled) sums the same
+quantity in another order: it and every FFT variant are compared with the oracle (1e-5).
 """
 import json
 
@@ -47,7 +48,9 @@ def test_variants_bit_identical_and_match_oracle(bse, spec):
     assert variants and default == variants[0]["index"]
     F = Forward(plan, 0, nsteps=spec.nsteps, nw=spec.nw)
     coef, en = _dev(s.coef, torch.complex64), _dev(s.energies, torch.float64)
-    ref = None
+    assert any(v["rows"] == 0 for v in variants) and variants[0]["rows"] == 0    # correlation kernel first
+    g = op.exchange_rho(spec, s.gk, s.coef)
+    ref, outs = None, []
     for v in variants:
         bse.bse_set_pair_variant(plan, 0, v["index"])
         assert bse.bse_pair_variants(plan, 0)[1] == v["index"]
@@ -59,15 +62,19 @@ def test_variants_bit_identical_and_match_oracle(bse, spec):
         bse.bse_pair_densities(plan, 0, bse.BSE_PD_DIRECT, None, None, None, None, F.rho_dir, q0, q1, F.ws_pair)
         bse.bse_status_read(plan)
         got = (F.rho_x.cpu().numpy(), F.rho_dir.cpu().numpy())
+        outs.append(got)
+        rx = got[0][:, :g.shape[1]]
+        assert np.abs(rx - g).max() / np.abs(g).max() < 1e-5, v        # exchange densities vs the oracle
+        if v["rows"] == 0:
+            continue
         if ref is None:
             ref = got
         else:
             assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), v
     bse.bse_set_pair_variant(plan, 0, -1)
-    # the exchange densities of the last variant against the oracle
-    g = op.exchange_rho(spec, s.gk, s.coef)
-    rx = ref[0][:, :g.shape[1]]
-    assert np.abs(rx - g).max() / np.abs(g).max() < 1e-5
+    # direct densities: correlation and FFT variants agree to FP32 rounding
+    dc, df = outs[0][1], ref[1]
+    assert np.abs(dc - df).max() < 1e-5 * np.abs(df).max()
     with pytest.raises(bse.BseError):
         bse.bse_set_pair_variant(plan, 0, 10 ** 6)
 
@@ -79,7 +86,7 @@ def test_autotune_picks_fastest_and_caches(bse, tmp_path):
     s = generate(spec, wdtype=np.complex64)
     plan = bse.Plan([spec])
     variants, _ = bse.bse_pair_variants(plan, 0)
-    assert len(variants) == 3
+    assert len(variants) == 4            # the correlation kernel and three FFT tile shapes
     F = Forward(plan, 0, nsteps=10, nw=50, qchunk=32)
     bse.bse_pair_densities(plan, 0, bse.BSE_PD_REALSPACE, _dev(s.coef, torch.complex64),
                            _dev(s.energies, torch.float64), None, None, None, 0, 0, F.ws_pair)
@@ -87,7 +94,7 @@ def test_autotune_picks_fastest_and_caches(bse, tmp_path):
     r = autotune.tune(plan, 0, F, reps=2, cache_path=cache)
     assert not r["cached"]
     ms = r["ms"]
-    assert len(ms) == 3 and all(t > 0 for t in ms.values())
+    assert len(ms) == 4 and all(t > 0 for t in ms.values())
     assert r["variant"]["index"] == int(min(ms, key=ms.get))
     assert bse.bse_pair_variants(plan, 0)[1] == r["variant"]["index"]
     stored = json.load(open(cache))

@@ -129,9 +129,11 @@ def test_fcc12_full_size_sampled(bse):
     _sum_rule(bse, plan, F, s.spec, P, 60)
 
 
+@pytest.mark.parametrize("method", ["correlation", "fft"])
 @pytest.mark.parametrize("name", ["g48", "hex", "hex_dirac"])
-def test_grid_variant_full_parity(bse, name):
-    """Every compiled FFT variant against the full oracle build and Haydock on a small cell."""
+def test_grid_variant_full_parity(bse, name, method):
+    """The plane-wave correlation kernel and the first compiled FFT variant of each grid against the full
+    oracle build and Haydock on a small cell."""
     from paper_1206_3518_gb300.pipeline import Forward
     if name == "g48":
         spec = config_spec("fcc_12x12x12_4v4c").replace(name="g48", nk=(2, 2, 2), nsteps=20, nw=200)
@@ -140,6 +142,9 @@ def test_grid_variant_full_parity(bse, name):
         spec = base.replace(name=name, nk=(6, 6, 1), nsteps=20, nw=200)
     s = generate(spec)
     plan = bse.Plan([spec])
+    variants, _ = bse.bse_pair_variants(plan, 0)
+    v = next(x for x in variants if (x["rows"] == 0) == (method == "correlation"))
+    bse.bse_set_pair_variant(plan, 0, v["index"])
     F = Forward(plan, 0, nsteps=spec.nsteps, nw=spec.nw)
     F.build(_dev(s.coef, torch.complex64), _dev(s.energies, torch.float64), _dev(s.W, torch.complex64), spec.delta)
     eps = F.spectrum(_dev(s.omega, torch.float64), spec.eta).cpu().numpy()
@@ -153,7 +158,11 @@ def test_grid_variant_full_parity(bse, name):
     off = ~np.eye(spec.dim, dtype=bool)
     assert np.abs(Hg - H)[off].max() / np.abs(H[off]).max() < 1e-5
     ref = osp.eps2_haydock(spec, H, Pv, s.omega, spec.eta, spec.nsteps)[0]
-    assert np.abs(eps - ref).max() / ref.max() < 1e-5
+    # floor set by storing H in FP32 (from the oracle alone): these cells' eps_2 moves by ~2e-5 of its
+    # peak under a random Hermitian change of 1e-7 max|H|, so an FP32 pipeline is held to 10x that floor
+    r32 = osp.eps2_haydock(spec, H.astype(np.complex64).astype(np.complex128), Pv, s.omega, spec.eta, spec.nsteps)[0]
+    floor = np.abs(r32 - ref).max() / ref.max()
+    assert np.abs(eps - ref).max() / ref.max() < max(1e-5, 10.0 * floor)
 
 
 def test_fcc12_mixed_precision_sampled(bse):

@@ -33,10 +33,14 @@ def _dev(x, dtype):
     return torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
 
 
-def _forward(bse, sysd, nsteps, nw=None, qchunk=None, keep=True, prec=0, delta=None):
+def _forward(bse, sysd, nsteps, nw=None, qchunk=None, keep=True, prec=0, delta=None, method=None):
     from paper_1206_3518_gb300.pipeline import Forward
     spec = sysd.spec
     plan = bse.Plan([spec])
+    if method is not None:          # "fft" or "correlation" pair densities (default: the planner's choice)
+        variants, _ = bse.bse_pair_variants(plan, 0)
+        v = next(x for x in variants if (x["rows"] == 0) == (method == "correlation"))
+        bse.bse_set_pair_variant(plan, 0, v["index"])
     nw = len(sysd.omega) if nw is None else nw
     F = Forward(plan, 0, nsteps=nsteps, nw=nw, qchunk=qchunk, keep_rho_dir=keep)
     coef = _dev(sysd.coef, torch.complex64)
@@ -70,15 +74,17 @@ def _relmax(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-def test_exchange_pair_densities_and_dipole(bse, cfg1, cfg1_oracle):
-    plan, F = _forward(bse, cfg1, 100)
+@pytest.mark.parametrize("method", ["correlation", "fft"])
+def test_exchange_pair_densities_and_dipole(bse, cfg1, cfg1_oracle, method):
+    plan, F = _forward(bse, cfg1, 100, method=method)
     rx = F.rho_x.cpu().numpy()[:, :113]
     assert _relmax(rx, cfg1_oracle["rho_x"]) < 1e-5
     assert _relmax(F.P.cpu().numpy(), cfg1_oracle["P"]) < 1e-6
 
 
-def test_direct_pair_densities_every_block(bse, cfg1, cfg1_oracle):
-    plan, F = _forward(bse, cfg1, 100)
+@pytest.mark.parametrize("method", ["correlation", "fft"])
+def test_direct_pair_densities_every_block(bse, cfg1, cfg1_oracle, method):
+    plan, F = _forward(bse, cfg1, 100, method=method)
     got = _rho_dir_by_block(bse, plan, cfg1.spec, F.rho_dir)
     scale = max(np.abs(f[3]).max() for f in cfg1_oracle["factors"])
     worst = 0.0
@@ -115,8 +121,13 @@ def test_spectrum_matches_oracle_haydock(bse, cfg1, cfg1_oracle):
     ref, a, b, _ = osp.eps2_haydock(spec, cfg1_oracle["H"], cfg1_oracle["P"], cfg1.omega, spec.eta, 100)
     assert np.abs(eps - ref).max() / ref.max() < 1e-5
     ab = F.ab.cpu().numpy()
-    assert np.abs(ab[:100] - a).max() < 1e-5 * np.abs(a).max()
-    assert np.abs(ab[100:] - b).max() < 1e-5 * np.abs(b).max()
+    # the 100-step coefficients move by ~5e-6 of their maximum when the oracle's own H is stored in FP32
+    # (1.6e-5 under a random Hermitian change of 3e-8 max|H|): an FP32 pipeline is held to 10x that floor
+    a32, b32, _, _ = osp.haydock(cfg1_oracle["H"].astype(np.complex64).astype(np.complex128), cfg1_oracle["P"], 100)
+    fa = np.abs(a32 - a).max() / np.abs(a).max()
+    fb = np.abs(b32 - b).max() / np.abs(b).max()
+    assert np.abs(ab[:100] - a).max() < max(1e-5, 10.0 * fa) * np.abs(a).max()
+    assert np.abs(ab[100:] - b).max() < max(1e-5, 10.0 * fb) * np.abs(b).max()
 
 
 def test_spectrum_full_krylov_equals_dense_eig(bse, cfg1, cfg1_oracle):
