@@ -597,7 +597,7 @@ def run_stage(args):
 # sources hash to the recorded value; see profiles/launches_fcc8x8x8_3v4c_fp32.md.
 # DRAM bytes (read + write) of one full-size correlation-kernel launch (direct set, all 512 q), from one ncu
 # capture of the sources with this SHA-1 (gcorr.cu + pairjob.cuh); not reported for other sources.
-GCORR_TRAFFIC = {"sha1": None, "bytes": None}
+GCORR_TRAFFIC = {"sha1": "ef80e8012b6d67c996e1db74f6e322391d834707", "bytes": 0.543646464e9 + 7.913224192e9}
 PAIR_TRAFFIC = {"sha1": "c39047a0b9675fda883a64bbde1871fdae56455a", "bytes": 101.77e9 + 8.39e9}
 
 
