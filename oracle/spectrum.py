@@ -18,8 +18,13 @@ e-h pairs gives, with P the conjugated k.p pair density divided by |q|,
   no terminator.  Breakdown: b_{j+1} <= 1e-10 |H v_j| stops the recursion (the
   Krylov space is invariant, so the truncated fraction is exact).
 
+``ritz``: eigenvalues and first-component weights of the tridiagonal (the pole
+expansion of g), i.e. exciton energies and normalised oscillator strengths.
+
 Pinned by tests/test_oracle_spectrum.py: dense == Haydock(N = dim) to 1e-10,
-kernel-off closed form, moment identities, rigid scissor shift.
+kernel-off closed form, moment identities, rigid scissor shift; the Ritz pairs
+against the dense eigenvalues of T, their moments, the pole expansion of the
+continued fraction, and the eigenpairs of H at full Krylov dimension.
 """
 from __future__ import annotations
 
@@ -93,3 +98,14 @@ def eps2_haydock(spec, H, P, omega, eta, nsteps):
     a, b, done, _ = haydock(H, P, nsteps)
     g = continued_fraction(a, b, omega + 1j * eta)
     return -prefactor(spec) * np.vdot(P, P).real * g.imag, a, b, done
+
+
+def ritz(a, b):
+    """Eigenvalues theta_i (ascending) and weights w_i = (first eigenvector component)^2 of the Lanczos
+    tridiagonal T (diagonal a, off-diagonal b[1:]): the poles and residues of g(z) = sum_i w_i/(z - theta_i),
+    i.e. exciton energies and normalised oscillator strengths |P^H A_l|^2/|P|^2 of the converged states."""
+    n = len(a)
+    if n == 1:
+        return np.array([a[0]]), np.array([1.0])
+    th, y = scipy.linalg.eigh_tridiagonal(np.asarray(a, dtype=np.float64), np.asarray(b[1:n], dtype=np.float64))
+    return th, y[0, :] ** 2

@@ -80,3 +80,29 @@ def test_breakdown_on_invariant_subspace_is_exact(cfg1):
     assert done == 12
     ref = osp.eps2_dense(spec, H, P, w, 0.004)
     assert np.abs(got - ref).max() / ref.max() < 1e-10
+
+
+def test_ritz_pairs_pinned(cfg1, cfg1_oracle):
+    """Ritz values/weights of the Haydock tridiagonal: dense eigenvalues of T, sum w = 1,
+    sum w theta = a_0, sum w theta^2 = a_0^2 + b_1^2, the pole expansion equals the continued
+    fraction, and at full Krylov dimension they are H's eigenvalues with weights |P^H A|^2/|P|^2."""
+    H, P = cfg1_oracle["H"], cfg1_oracle["P"]
+    a, b, done, _ = osp.haydock(H, P, 60)
+    th, w = osp.ritz(a, b)
+    T = np.diag(a) + np.diag(b[1:], 1) + np.diag(b[1:], -1)
+    assert np.abs(np.sort(np.linalg.eigvalsh(T)) - th).max() < 1e-12
+    assert abs(w.sum() - 1.0) < 1e-12
+    assert abs(w @ th - a[0]) < 1e-12
+    assert abs(w @ th ** 2 - (a[0] ** 2 + b[1] ** 2)) < 1e-12
+    z = np.linspace(0.0, 0.5, 41) + 1j * 0.01
+    g = osp.continued_fraction(a, b, z)
+    assert np.abs((w[None, :] / (z[:, None] - th[None, :])).sum(1) - g).max() < 1e-9 * np.abs(g).max()
+    # full Krylov dimension: the Ritz pairs are H's eigenpairs with nonzero weight
+    a, b, done, _ = osp.haydock(H, P, H.shape[0])
+    th, w = osp.ritz(a, b)
+    e, v = np.linalg.eigh(H)
+    wt = np.abs(np.conj(P) @ v) ** 2 / np.vdot(P, P).real
+    keep = w > 1e-8
+    for t, x in zip(th[keep], w[keep]):
+        i = np.argmin(np.abs(e - t))
+        assert abs(e[i] - t) < 1e-9 and abs(wt[i] - x) < 1e-7 * max(1.0, x)
