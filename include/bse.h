@@ -65,7 +65,8 @@ typedef enum {
   BSE_WS_BACKWARD = 3,  /* bse_spectrum_backward: basis, dL/dH, chain products */
   BSE_WS_SCREEN = 4,    /* bse_screening: dielectric matrices of one q chunk (arg = chunk) */
   BSE_WS_COUPLING = 5,  /* bse_build_coupling: W.rho_cv' of one q chunk (arg = chunk; 0 = INIT only) */
-  BSE_WS_COUPLED = 6    /* bse_spectrum_coupled: basis, vectors, partial sums (arg = nsteps) */
+  BSE_WS_COUPLED = 6,   /* bse_spectrum_coupled: basis, vectors, partial sums (arg = nsteps) */
+  BSE_WS_RITZ = 7       /* bse_ritz: per-Ritz-value scratch (arg = nsteps <= 4096; plan/system unused) */
 } bse_ws_kind;
 
 /* Stage flags for bse_pair_densities and bse_build_kernel. */
@@ -229,6 +230,23 @@ bse_status bse_spectrum(bse_plan* plan, int s, const void* H, const void* P, int
                         const double* omega, int nw, double eta,
                         double* eps2, double* ab, int* steps_done,
                         void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Exciton energies and oscillator strengths from a Haydock recursion: the eigenvalues theta_i of its
+ * tridiagonal T (diagonal a_j, off-diagonal b_j) and the weights w_i = (first component of the
+ * normalised eigenvector)^2, the poles and residues of g(z) = sum_i w_i/(z - theta_i).  Converged Ritz
+ * pairs are eigenpairs of H: E_l and |P^H A_l|^2/|P|^2 (the spectral representation of Eqs. resolvent
+ * and epsilon_chi_bar); sum_i w_i = 1.
+ * ab         float64 [2*nsteps] as written by bse_spectrum (a_0..a_{n-1}, then b_0 = 0, b_1..b_{n-1}).
+ * steps_done int32 [1] as written by bse_spectrum; n = min(steps_done, nsteps).
+ * theta      float64 [nsteps] ascending (entries >= n set to 0);  weight float64 [nsteps].
+ * ws         bse_workspace_size(BSE_WS_RITZ, nsteps) bytes (any plan and system).
+ * One thread per Ritz value in FP64: bisection on Sturm counts, inverse iteration with partial
+ * pivoting.  No device-side waits; capturable.  Errors: BSE_ERR_ARG (nsteps outside [1, 4096]),
+ * BSE_ERR_WORKSPACE.
+ */
+bse_status bse_ritz(const double* ab, const int* steps_done, int nsteps, double* theta, double* weight, void* ws,
+                    size_t ws_bytes, void* stream);
 
 /*
  * A7 + A8 for a batch of n <= 24 systems of one plan in ONE persistent cooperative

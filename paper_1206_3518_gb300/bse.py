@@ -21,7 +21,7 @@ BSE_LATTICE_FCC, BSE_LATTICE_HEX = 0, 1
 BSE_COULOMB_3D, BSE_COULOMB_SLAB = 0, 1
 BSE_PREC_FP32, BSE_PREC_BF16X3 = 0, 1
 BSE_WS_PAIR, BSE_WS_KERNEL, BSE_WS_SPECTRUM, BSE_WS_BACKWARD, BSE_WS_SCREEN = 0, 1, 2, 3, 4
-BSE_WS_COUPLING, BSE_WS_COUPLED = 5, 6
+BSE_WS_COUPLING, BSE_WS_COUPLED, BSE_WS_RITZ = 5, 6, 7
 BSE_PD_REALSPACE, BSE_PD_EXCHANGE, BSE_PD_DIRECT, BSE_PD_CHI0, BSE_PD_COUPLING = 1, 2, 4, 8, 16
 BSE_BK_INIT, BSE_BK_DIRECT, BSE_BK_MIRROR = 1, 2, 4
 BSE_BC_INIT, BSE_BC_DIRECT, BSE_BC_MIRROR = 1, 2, 4
@@ -31,7 +31,7 @@ EXPORTED = [
     "bse_pair_blocks", "bse_workspace_size", "bse_rho_dir_count", "bse_pair_densities",
     "bse_build_kernel", "bse_apply_H", "bse_spectrum", "bse_spectrum_static", "bse_spectrum_batch", "bse_spectrum_backward", "bse_status_read",
     "bse_pair_variants", "bse_set_pair_variant", "bse_autotune_pair", "bse_set_wait_limit", "bse_screening",
-    "bse_rho_cpl_count", "bse_build_coupling", "bse_spectrum_coupled",
+    "bse_rho_cpl_count", "bse_build_coupling", "bse_spectrum_coupled", "bse_ritz",
 ]
 
 
@@ -102,6 +102,7 @@ def load():
     lib.bse_rho_cpl_count.argtypes = [vp, i, i, i, ctypes.POINTER(ll)]
     lib.bse_build_coupling.argtypes = [vp, i, u, vp, vp, i, i, vp, i, vp, vp, sz, vp]
     lib.bse_spectrum_coupled.argtypes = [vp, i, vp, vp, vp, i, vp, i, d, vp, vp, vp, vp, sz, vp]
+    lib.bse_ritz.argtypes = [vp, vp, i, vp, vp, vp, sz, vp]
     for name in EXPORTED:
         if name != "bse_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -324,3 +325,9 @@ def bse_spectrum_coupled(plan, s, A, Bm, P, nsteps, omega, eta, eps2, b, steps_d
     _check(load().bse_spectrum_coupled(plan.handle, s, _ptr(A), _ptr(Bm), _ptr(P), int(nsteps), _ptr(omega),
                                        omega.numel(), float(eta), _ptr(eps2), _ptr(b), _ptr(steps_done), _ptr(ws),
                                        _nbytes(ws), _stream()))
+
+
+def bse_ritz(ab, steps_done, nsteps, theta, weight, ws):
+    """Ritz values (exciton energies) and weights (normalised oscillator strengths) of a Haydock recursion."""
+    _check(load().bse_ritz(_ptr(ab), _ptr(steps_done), int(nsteps), _ptr(theta), _ptr(weight), _ptr(ws), _nbytes(ws),
+                           _stream()))

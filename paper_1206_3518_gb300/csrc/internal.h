@@ -97,6 +97,9 @@ int launch_coupling_direct_range(const DevSys& d, const void* rho_cpl, int q_beg
                                  int* status, void* stream);
 int launch_coupling_mirror(const DevSys& d, void* Bm, void* stream);
 size_t coupled_ws_bytes(const DevSys& d, long long nsteps);
+size_t ritz_ws_bytes(long long nsteps);
+int launch_ritz(const double* ab, const int* steps_done, int nsteps, double* theta, double* weight, void* ws,
+                void* stream);
 int launch_spectrum_coupled(const DevSys& d, const void* A, const void* Bm, const void* P, int nsteps,
                             const double* omega, int nw, double eta, double* eps2, double* b, int* steps_done,
                             void* ws, int* status, void* stream);

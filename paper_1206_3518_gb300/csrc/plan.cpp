@@ -465,6 +465,10 @@ bse_status bse_workspace_size(const bse_plan* plan, int s, int kind, long long a
       if (arg < 1) return set_error(BSE_ERR_ARG, "nsteps < 1");
       *bytes = coupled_ws_bytes(d, arg);
       return BSE_OK;
+    case BSE_WS_RITZ:
+      if (arg < 1 || arg > 4096) return set_error(BSE_ERR_ARG, "nsteps outside [1, 4096]");
+      *bytes = ritz_ws_bytes(arg);
+      return BSE_OK;
   }
   return set_error(BSE_ERR_ARG, "unknown workspace kind");
 }
@@ -810,6 +814,14 @@ bse_status bse_spectrum_coupled(bse_plan* plan, int s, const void* A, const void
                                         stream);
   if (e == -2) return set_error(BSE_ERR_UNSUPPORTED, "coupled spectrum is built for dim <= 65536");
   return cuda_check(e, "coupled spectrum");
+}
+
+bse_status bse_ritz(const double* ab, const int* steps_done, int nsteps, double* theta, double* weight, void* ws,
+                    size_t ws_bytes, void* stream) {
+  if (!ab || !steps_done || !theta || !weight || nsteps < 1 || nsteps > 4096)
+    return set_error(BSE_ERR_ARG, "ritz needs ab, steps_done, theta, weight and 1 <= nsteps <= 4096");
+  if (!ws || ws_bytes < ritz_ws_bytes(nsteps)) return set_error(BSE_ERR_WORKSPACE, "ritz workspace too small");
+  return cuda_check(launch_ritz(ab, steps_done, nsteps, theta, weight, ws, stream), "ritz");
 }
 
 bse_status bse_set_wait_limit(unsigned long long ns) {
