@@ -16,4 +16,4 @@ Parity status per function is stated in each module header; every function is
 pinned by ``tests/test_oracle_*.py`` against closed forms, brute force,
 invariants or textbook limits.
 """
-from . import geometry, pair, kernel, spectrum, adjoint, screening, coupling  # noqa: F401
+from . import geometry, pair, kernel, spectrum, adjoint, screening, coupling, symmetry  # noqa: F401
