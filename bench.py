@@ -295,6 +295,23 @@ def run_ours(args):
         step()       # restore the step's own state
         torch.cuda.synchronize()
 
+    # q-point symmetry (Sec. III A): W of the irreducible points only, unfolded on the device
+    nops, ibz_q, _, _ = bse.bse_symmetry(plan, 0)
+    W_ibz = W[torch.as_tensor(ibz_q.astype(np.int64), device=dev)].contiguous()
+    W_full = torch.empty_like(W)
+    bse.bse_unfold_w(plan, 0, W_ibz, W_full, 0, inf["nq"])
+    torch.cuda.synchronize()
+    u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    u0.record(stream)
+    bse.bse_unfold_w(plan, 0, W_ibz, W_full, 0, inf["nq"])
+    u1.record(stream)
+    torch.cuda.synchronize()
+    bse.bse_status_read(plan)
+    symmetry = {"ops": nops, "irreducible_q": int(len(ibz_q)), "q": inf["nq"],
+                "w_bytes_irreducible": W_ibz.numel() * 8, "w_bytes_full": W.numel() * 8,
+                "unfold_ms": u0.elapsed_time(u1)}
+    del W_ibz, W_full
+
     peaks, src = _peaks()
     coupled = None
     if not args.no_coupled and world == 1:
@@ -326,6 +343,7 @@ def run_ours(args):
         "batch": batch,
         "screening": screening,
         "coupled": coupled,
+        "symmetry": symmetry,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(spec, s, budget_s=args.cpu_budget)

@@ -232,6 +232,25 @@ bse_status bse_spectrum(bse_plan* plan, int s, const void* H, const void* P, int
                         void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * q-point symmetry (Sec. III A).  The planner finds the point group of the lattice as integer
+ * matrices R on reduced reciprocal coordinates (R^T M R = M for the reciprocal metric M, mapping the
+ * k mesh onto itself; symmorphic, no fractional translations), ordered identity first then by
+ * ascending row-major entries, and reduces the q mesh under R and time reversal: q visited in
+ * ascending index, an unassigned q becomes irreducible and every image s R q (s = +1, then -1, for
+ * each R in order) not yet assigned maps to it with G0 = q - s R q_IBZ.
+ * bse_symmetry (host or device plan): *nops, *nibz; ibz int32 [nq] (first nibz entries: the
+ * irreducible q indices, ascending); qmap int32 [nq][6] = (irreducible index, operation, time
+ * reversal, G0x, G0y, G0z); perm int32 [nq][ng_max]: position on the sphere of q_IBZ of
+ * s R^-1 (g_p + G0) for each point p of the sphere of q (-1 past the sphere).  Outputs may be NULL.
+ * bse_unfold_w: W complex64 [nq][ng_max][ng_max] for q in [q_begin, q_end) from W_ibz complex64
+ * [nibz][ng_max][ng_max] (row i belongs to ibz[i]): W_pp'(q) = W_ibz[perm p][perm p'], conjugated
+ * for time reversal (Sec. III A); entries past the sphere are zero.  Errors: BSE_ERR_ARG.
+ */
+bse_status bse_symmetry(const bse_plan* plan, int s, int* nops, int* nibz, int32_t* ibz, int32_t* qmap,
+                        int32_t* perm);
+bse_status bse_unfold_w(bse_plan* plan, int s, const void* W_ibz, void* W, int q_begin, int q_end, void* stream);
+
+/*
  * Exciton energies and oscillator strengths from a Haydock recursion: the eigenvalues theta_i of its
  * tridiagonal T (diagonal a_j, off-diagonal b_j) and the weights w_i = (first component of the
  * normalised eigenvector)^2, the poles and residues of g(z) = sum_i w_i/(z - theta_i).  Converged Ritz

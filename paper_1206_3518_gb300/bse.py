@@ -31,7 +31,7 @@ EXPORTED = [
     "bse_pair_blocks", "bse_workspace_size", "bse_rho_dir_count", "bse_pair_densities",
     "bse_build_kernel", "bse_apply_H", "bse_spectrum", "bse_spectrum_static", "bse_spectrum_batch", "bse_spectrum_backward", "bse_status_read",
     "bse_pair_variants", "bse_set_pair_variant", "bse_autotune_pair", "bse_set_wait_limit", "bse_screening",
-    "bse_rho_cpl_count", "bse_build_coupling", "bse_spectrum_coupled", "bse_ritz",
+    "bse_rho_cpl_count", "bse_build_coupling", "bse_spectrum_coupled", "bse_ritz", "bse_symmetry", "bse_unfold_w",
 ]
 
 
@@ -103,6 +103,8 @@ def load():
     lib.bse_build_coupling.argtypes = [vp, i, u, vp, vp, i, i, vp, i, vp, vp, sz, vp]
     lib.bse_spectrum_coupled.argtypes = [vp, i, vp, vp, vp, i, vp, i, d, vp, vp, vp, vp, sz, vp]
     lib.bse_ritz.argtypes = [vp, vp, i, vp, vp, vp, sz, vp]
+    lib.bse_symmetry.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), vp, vp, vp]
+    lib.bse_unfold_w.argtypes = [vp, i, vp, vp, i, i, vp]
     for name in EXPORTED:
         if name != "bse_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -331,3 +333,22 @@ def bse_ritz(ab, steps_done, nsteps, theta, weight, ws):
     """Ritz values (exciton energies) and weights (normalised oscillator strengths) of a Haydock recursion."""
     _check(load().bse_ritz(_ptr(ab), _ptr(steps_done), int(nsteps), _ptr(theta), _ptr(weight), _ptr(ws), _nbytes(ws),
                            _stream()))
+
+
+def bse_symmetry(plan, s):
+    """(nops, ibz [nibz], qmap [nq][6], perm [nq][ng_max]) of the plan's q-point symmetry reduction."""
+    import numpy as np
+    inf = plan.info(s)
+    nq, ng = inf["nq"], inf["ng_max"]
+    nops, nibz = ctypes.c_int(), ctypes.c_int()
+    ibz = np.zeros(nq, dtype=np.int32)
+    qmap = np.zeros((nq, 6), dtype=np.int32)
+    perm = np.zeros((nq, ng), dtype=np.int32)
+    _check(load().bse_symmetry(plan.handle, s, ctypes.byref(nops), ctypes.byref(nibz), ibz.ctypes.data_as(ctypes.c_void_p),
+                               qmap.ctypes.data_as(ctypes.c_void_p), perm.ctypes.data_as(ctypes.c_void_p)))
+    return int(nops.value), ibz[: nibz.value].copy(), qmap, perm
+
+
+def bse_unfold_w(plan, s, W_ibz, W, q_begin, q_end):
+    """W on the q range from W on the irreducible points (Sec. III A)."""
+    _check(load().bse_unfold_w(plan.handle, s, _ptr(W_ibz), _ptr(W), q_begin, q_end, _stream()))

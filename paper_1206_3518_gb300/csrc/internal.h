@@ -1,6 +1,7 @@
 // Internal declarations shared by the host planner, the C-ABI glue and the CUDA kernels.
 #pragma once
 
+#include <array>
 #include <cstdint>
 #include <vector_types.h>
 #include <string>
@@ -33,6 +34,9 @@ struct DevSys {
   long long nblocks;
   int pair_variant;               // index of the pair-kernel variant chosen for this system, -1 = first valid
   const int* gminus0;             // [ng0] index of -G on the q = 0 sphere (-1 if absent)
+  const int* qperm;               // [nq][ng_max] sphere map of q onto its irreducible point (-1 padded)
+  const int2* qsym;               // [nq] (irreducible index, time reversal)
+  int nibz;
 };
 
 struct SysPlan {
@@ -42,6 +46,10 @@ struct SysPlan {
   std::vector<int32_t> blocks;                 // host (ik, ik2, iq, g0x, g0y, g0z) per block
   std::vector<long long> qblk_off, qvec_off;
   bool gminus0_complete = false;  // every G of the q = 0 sphere has -G on it
+  // q-point symmetry (Sec. III A): operations (row-major integer 3x3 on reduced reciprocal
+  // coordinates), irreducible q points, per q (iq_ibz index, op, tr, G0x, G0y, G0z), sphere maps
+  std::vector<std::array<int, 9>> ops;
+  std::vector<int> ibz, qmap, qperm;
   void* dmem = nullptr;           // one device allocation holding every table
 };
 
@@ -98,6 +106,7 @@ int launch_coupling_direct_range(const DevSys& d, const void* rho_cpl, int q_beg
 int launch_coupling_mirror(const DevSys& d, void* Bm, void* stream);
 size_t coupled_ws_bytes(const DevSys& d, long long nsteps);
 size_t ritz_ws_bytes(long long nsteps);
+int launch_unfold_w(const DevSys& d, const void* W_ibz, void* W, int q_begin, int q_end, void* stream);
 int launch_ritz(const double* ab, const int* steps_done, int nsteps, double* theta, double* weight, void* ws,
                 void* stream);
 int launch_spectrum_coupled(const DevSys& d, const void* A, const void* Bm, const void* P, int nsteps,

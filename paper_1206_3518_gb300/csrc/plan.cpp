@@ -263,6 +263,106 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
     h_xs[t] = (float)std::sqrt(2.0 * d.norm * v);
   }
 
+  // ---- q-point symmetry (Sec. III A) ----
+  // Operations: integer matrices R on reduced reciprocal coordinates with R^T M R = M (M the
+  // reciprocal metric) that map the mesh onto itself; identity first, then ascending row-major
+  // entries.  Irreducible points and maps: q visited by ascending index, an unassigned q becomes
+  // irreducible, each operation in order assigns its image s R q (s = +1, then -1) if unassigned,
+  // with G0 = q' - s R q_IBZ.  Sphere map of q: G -> s R^-1 (G + G0) on the sphere of q_IBZ.
+  {
+    double M[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) M[i][j] = b[i][0] * b[j][0] + b[i][1] * b[j][1] + b[i][2] * b[j][2];
+    double mmax = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) mmax = std::max(mmax, std::fabs(M[i][j]));
+    std::vector<std::array<int, 9>> ops;
+    std::array<int, 9> R;
+    for (int code = 0; code < 19683; ++code) {
+      int c = code;
+      for (int t = 8; t >= 0; --t) {         // entries in -1, 0, 1, lexicographic with entry 0 most significant
+        R[t] = c % 3 - 1;
+        c /= 3;
+      }
+      const int det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                      R[2] * (R[3] * R[7] - R[4] * R[6]);
+      if (det != 1 && det != -1) continue;
+      bool ok = true;
+      for (int i = 0; i < 3 && ok; ++i)
+        for (int j = 0; j < 3 && ok; ++j) {
+          double v = 0.0;                     // (R^T M R)_ij
+          for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) v += R[3 * k + i] * M[k][l] * R[3 * l + j];
+          ok = std::fabs(v - M[i][j]) <= 1e-9 * mmax;
+        }
+      for (int i = 0; i < 3 && ok; ++i)       // image of e_j / n_j on the mesh: R_ij n_i / n_j integral
+        for (int j = 0; j < 3 && ok; ++j) ok = (R[3 * i + j] * s.nk[i]) % s.nk[j] == 0;
+      if (ok) ops.push_back(R);
+    }
+    const std::array<int, 9> ident = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    std::vector<std::array<int, 9>> sorted;
+    sorted.push_back(ident);
+    for (const auto& r : ops)
+      if (r != ident) sorted.push_back(r);    // enumeration order is already lexicographic
+    sp.ops = sorted;
+    const int nops = (int)sorted.size();
+    sp.qmap.assign((size_t)6 * nkpt, -1);
+    sp.ibz.clear();
+    for (int iq = 0; iq < nkpt; ++iq) {
+      if (sp.qmap[6 * iq] >= 0) continue;
+      sp.ibz.push_back(iq);
+      int o[3];
+      offs(iq, o);
+      for (int io = 0; io < nops; ++io)
+        for (int tr = 0; tr < 2; ++tr) {
+          const auto& r = sorted[io];
+          int img[3], fold[3], g0[3];
+          for (int i = 0; i < 3; ++i) {
+            img[i] = (tr ? -1 : 1) * (r[3 * i] * o[0] + r[3 * i + 1] * o[1] + r[3 * i + 2] * o[2]);
+            fold[i] = ((img[i] % s.nk[i]) + s.nk[i]) % s.nk[i];
+            g0[i] = (fold[i] - img[i]) / s.nk[i];
+          }
+          const int iq2 = (fold[0] * nk2 + fold[1]) * nk3 + fold[2];
+          if (sp.qmap[6 * iq2] >= 0) continue;
+          int* m = &sp.qmap[6 * iq2];
+          m[0] = (int)sp.ibz.size() - 1;
+          m[1] = io;
+          m[2] = tr;
+          m[3] = g0[0];
+          m[4] = g0[1];
+          m[5] = g0[2];
+        }
+    }
+    sp.qperm.assign((size_t)nkpt * ng_max, -1);
+    auto key = [](int a, int b2, int c) { return ((long long)(a + 512) << 20) | ((long long)(b2 + 512) << 10) | (c + 512); };
+    std::vector<std::unordered_map<long long, int>> pos(sp.ibz.size());
+    for (size_t j = 0; j < sp.ibz.size(); ++j) {
+      const auto& g = sp.gq[sp.ibz[j]];
+      for (int t = 0; t < (int)g.size() / 3; ++t) pos[j][key(g[3 * t], g[3 * t + 1], g[3 * t + 2])] = t;
+    }
+    for (int iq = 0; iq < nkpt; ++iq) {
+      const int* m = &sp.qmap[6 * iq];
+      const auto& r = sorted[m[1]];
+      // R^-1 = adj(R) / det(R), integral
+      const int det = r[0] * (r[4] * r[8] - r[5] * r[7]) - r[1] * (r[3] * r[8] - r[5] * r[6]) +
+                      r[2] * (r[3] * r[7] - r[4] * r[6]);
+      int ri[9] = {(r[4] * r[8] - r[5] * r[7]) * det, (r[2] * r[7] - r[1] * r[8]) * det, (r[1] * r[5] - r[2] * r[4]) * det,
+                   (r[5] * r[6] - r[3] * r[8]) * det, (r[0] * r[8] - r[2] * r[6]) * det, (r[2] * r[3] - r[0] * r[5]) * det,
+                   (r[3] * r[7] - r[4] * r[6]) * det, (r[1] * r[6] - r[0] * r[7]) * det, (r[0] * r[4] - r[1] * r[3]) * det};
+      const int sg = m[2] ? -1 : 1;
+      const auto& g = sp.gq[iq];
+      for (int t = 0; t < (int)g.size() / 3; ++t) {
+        const int x[3] = {g[3 * t] + m[3], g[3 * t + 1] + m[4], g[3 * t + 2] + m[5]};
+        int y[3];
+        for (int i = 0; i < 3; ++i) y[i] = sg * (ri[3 * i] * x[0] + ri[3 * i + 1] * x[1] + ri[3 * i + 2] * x[2]);
+        auto it = pos[m[0]].find(key(y[0], y[1], y[2]));
+        if (it == pos[m[0]].end()) return set_error(BSE_ERR_ARG, "symmetry: sphere of q does not map onto its irreducible point");
+        sp.qperm[(size_t)iq * ng_max + t] = it->second;
+      }
+    }
+    d.nibz = (int)sp.ibz.size();
+  }
+
   // -G on the q = 0 sphere (coupling exchange, Bx)
   std::vector<int> h_gm0(d.ng0 > 0 ? d.ng0 : 1, -1);
   {
@@ -290,6 +390,10 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   const size_t o_bi = off; off = align256(off + h_blkidx.size() * sizeof(int));
   const size_t o_vsq = off; off = align256(off + h_vsq.size() * sizeof(float));
   const size_t o_gm0 = off; off = align256(off + h_gm0.size() * sizeof(int));
+  std::vector<int2> h_qsym(nkpt);
+  for (int iq = 0; iq < nkpt; ++iq) h_qsym[iq] = make_int2(sp.qmap[6 * iq], sp.qmap[6 * iq + 2]);
+  const size_t o_qp = off; off = align256(off + sp.qperm.size() * sizeof(int));
+  const size_t o_qs = off; off = align256(off + h_qsym.size() * sizeof(int2));
   char* base = nullptr;
   bse_status st = cuda_check(cudaMalloc((void**)&base, off), "cudaMalloc(plan tables)");
   if (st != BSE_OK) return st;
@@ -308,6 +412,8 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   if (!err) err = up(o_bi, h_blkidx.data(), h_blkidx.size() * sizeof(int));
   if (!err) err = up(o_vsq, h_vsq.data(), h_vsq.size() * sizeof(float));
   if (!err) err = up(o_gm0, h_gm0.data(), h_gm0.size() * sizeof(int));
+  if (!err) err = up(o_qp, sp.qperm.data(), sp.qperm.size() * sizeof(int));
+  if (!err) err = up(o_qs, h_qsym.data(), h_qsym.size() * sizeof(int2));
   if ((st = cuda_check(err, "cudaMemcpy(plan tables)")) != BSE_OK) return st;
   d.gk = (const char4*)(base + o_gk);
   d.npw = (const int*)(base + o_npw);
@@ -321,6 +427,8 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   d.blkidx = (const int*)(base + o_bi);
   d.vsq = (const float*)(base + o_vsq);
   d.gminus0 = (const int*)(base + o_gm0);
+  d.qperm = (const int*)(base + o_qp);
+  d.qsym = (const int2*)(base + o_qs);
   return BSE_OK;
 }
 
@@ -814,6 +922,27 @@ bse_status bse_spectrum_coupled(bse_plan* plan, int s, const void* A, const void
                                         stream);
   if (e == -2) return set_error(BSE_ERR_UNSUPPORTED, "coupled spectrum is built for dim <= 65536");
   return cuda_check(e, "coupled spectrum");
+}
+
+bse_status bse_symmetry(const bse_plan* plan, int s, int* nops, int* nibz, int32_t* ibz, int32_t* qmap,
+                        int32_t* perm) {
+  bse_status st = check_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const SysPlan& sp = plan->sys[s];
+  if (nops) *nops = (int)sp.ops.size();
+  if (nibz) *nibz = (int)sp.ibz.size();
+  if (ibz) std::memcpy(ibz, sp.ibz.data(), sp.ibz.size() * sizeof(int32_t));
+  if (qmap) std::memcpy(qmap, sp.qmap.data(), sp.qmap.size() * sizeof(int32_t));
+  if (perm) std::memcpy(perm, sp.qperm.data(), sp.qperm.size() * sizeof(int32_t));
+  return BSE_OK;
+}
+
+bse_status bse_unfold_w(bse_plan* plan, int s, const void* W_ibz, void* W, int q_begin, int q_end, void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const DevSys& d = plan->sys[s].d;
+  if (!W_ibz || !W || q_begin < 0 || q_end > d.nq || q_begin >= q_end) return set_error(BSE_ERR_ARG, "bad unfold arguments");
+  return cuda_check(launch_unfold_w(d, W_ibz, W, q_begin, q_end, stream), "unfold W");
 }
 
 bse_status bse_ritz(const double* ab, const int* steps_done, int nsteps, double* theta, double* weight, void* ws,

@@ -86,3 +86,23 @@ def test_host_only_plan_refuses_compute(bse, cfg1):
         bse.load().bse_apply_H(plan.handle, 0, None, None, None, 1, None)
         bse._check(bse.load().bse_apply_H(plan.handle, 0, None, None, None, 1, None))
     assert e.value.code == bse.BSE_ERR_ARG
+
+
+@pytest.mark.parametrize("name", ["fcc_4x4x4_3v3c", "fcc_8x8x8_3v4c", "hex6"])
+def test_symmetry_tables_bit_exact_vs_oracle(name):
+    """Point group order, irreducible q points, per-q maps and sphere permutations of the host planner
+    against oracle/symmetry.py (integer work: bit-exact)."""
+    from oracle import symmetry as sy
+    from paper_1206_3518_gb300 import bse
+    from synth import config_spec, slab_batch_specs
+    spec = slab_batch_specs(0)[5].replace(name="hex6", nk=(6, 6, 1)) if name == "hex6" else config_spec(name)
+    plan = bse.bse_plan_create_host([spec])
+    nops, ibz, qmap, perm = bse.bse_symmetry(plan, 0)
+    ops = sy.point_group(spec)
+    oibz, oqmap = sy.reduce_mesh(spec, ops)
+    assert nops == len(ops)
+    assert ibz.tolist() == list(oibz)
+    assert [tuple(r) for r in qmap.tolist()] == [tuple(m) for m in oqmap]
+    for iq in range(spec.nkpt):
+        p = sy.sphere_perm(spec, iq, oibz, oqmap, ops)
+        assert perm[iq, :len(p)].tolist() == p.tolist() and np.all(perm[iq, len(p):] == -1)
