@@ -10,13 +10,13 @@
 //
 // One CTA per job (decode_job of pairjob.cuh: the blocks of the direct and coupling sets, the
 // exchange set, or the (k, k+q) set of the screening), one thread per sphere point p of q.
-// Shared memory holds the job's coefficients at k (planar per band, plus a zero row), those at k'
+// Shared memory holds the job's coefficients at k (packed per G1, plus a zero row), those at k'
 // (packed per G2 for broadcast loads), and a dense index box of S(k) over the key range
 // G2 - G (per axis |.| <= fwf + fpair), whose entries outside the sphere point at the zero row.  The
 // inner loop runs over G2: one box lookup, a
-// gather of the k bands and a broadcast of the k' bands, then every band product of the job as FP32
-// complex multiply-adds; iterations in which no lane of a warp has a partner in S(k) are skipped.  The
-// G = 0 overlaps of the diagonal blocks are summed again in FP64.
+// gather of the k bands (one packed row, 128-bit loads), a broadcast of the k' bands, then every band
+// product of the job as FP32 complex multiply-adds.  The G = 0 overlaps of the diagonal blocks are
+// summed again in FP64.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -37,6 +37,9 @@ struct Shape {
   static constexpr int NA = KIND == 0 ? NV : NB;      // bands at k
   static constexpr int NK = KIND == 0 ? NC : NB;      // bands at k'
   static constexpr int NKP = (NK + 1) & ~1;           // packed row of k' bands (float4 loads)
+  // packed row of k bands: even, and an odd number of 16-byte units so that rows gathered by
+  // different lanes spread over the shared-memory banks
+  static constexpr int RS = (((NA + 1) & ~1) / 2) % 2 == 1 ? ((NA + 1) & ~1) : ((NA + 1) & ~1) + 2;
   static constexpr int P = KIND == 0 ? NV * NC : (KIND == 1 ? NV * NV + NC * NC : 2 * NV * NC);
   // band at k, band at k', output (0: out_v, 1: out_c), index within that output
   static constexpr int a(int p) {
@@ -60,7 +63,7 @@ struct Box {
 template <int NV, int NC, int KIND>
 size_t smem_bytes(const DevSys& d, const Box& bx) {
   using S = Shape<NV, NC, KIND>;
-  const size_t ca = (size_t)S::NA * (d.npw_max + 1) * sizeof(float2);
+  const size_t ca = (size_t)S::RS * (d.npw_max + 1) * sizeof(float2);
   const size_t cb = (size_t)d.npw_max * S::NKP * sizeof(float2);
   const size_t lin = (size_t)d.npw_max * sizeof(int);
   const size_t box = ((size_t)bx.n * sizeof(unsigned short) + 15) & ~(size_t)15;
@@ -71,14 +74,13 @@ size_t smem_bytes(const DevSys& d, const Box& bx) {
 // rho_nm^{kk}(0) are delta_nm (0 for the coupling set) up to rounding and meet the q = 0 head of W
 // (~1e4 Ha bohr^3 for the slab workloads).  One warp sums them again with FP64 accumulation.
 template <int NV, int NC, int KIND>
-__device__ __noinline__ void g0_overlaps(const float2* ca, const float2* cb2, int stride, int n2, const Job& jb,
-                                         int ng_max) {
+__device__ __noinline__ void g0_overlaps(const float2* ca, const float2* cb2, int n2, const Job& jb, int ng_max) {
   using S = Shape<NV, NC, KIND>;
   const int lane = threadIdx.x & 31;
   for (int q = 0; q < S::P; ++q) {
     double sr = 0.0, si = 0.0;
     for (int i = lane; i < n2; i += 32) {
-      const float2 x = ca[S::a(q) * stride + i], y = cb2[i * S::NKP + S::b(q)];
+      const float2 x = ca[i * S::RS + S::a(q)], y = cb2[i * S::NKP + S::b(q)];
       sr += (double)x.x * y.x + (double)x.y * y.y;        // conj(x) y
       si += (double)x.x * y.y - (double)x.y * y.x;
     }
@@ -103,9 +105,9 @@ __global__ __launch_bounds__(kGcMaxThreads) void gcorr_kernel(DevSys d, const fl
   Job jb;
   if (!decode_job(d, mode, true, q0, nqc, vbase, out, jb)) return;
   extern __shared__ __align__(16) float4 smv[];
-  const int stride = d.npw_max + 1;                    // planar k rows; index npw_max is the zero row
-  float2* ca = reinterpret_cast<float2*>(smv);
-  const size_t ca_bytes = (((size_t)NA * stride * sizeof(float2)) + 15) & ~(size_t)15;
+  constexpr int RS = S::RS;
+  float2* ca = reinterpret_cast<float2*>(smv);         // [npw_max + 1][RS]: k bands per G1; row npw_max is zero
+  const size_t ca_bytes = (((size_t)RS * (d.npw_max + 1) * sizeof(float2)) + 15) & ~(size_t)15;
   float4* cb = reinterpret_cast<float4*>(reinterpret_cast<char*>(smv) + ca_bytes);   // [npw_max][NKP/2]
   int* lin2 = reinterpret_cast<int*>(cb + (size_t)d.npw_max * (NKP / 2));
   unsigned short* box = reinterpret_cast<unsigned short*>(lin2 + d.npw_max);
@@ -114,9 +116,9 @@ __global__ __launch_bounds__(kGcMaxThreads) void gcorr_kernel(DevSys d, const fl
   const int n1 = d.npw[jb.k], n2 = d.npw[jb.k2];
 
   for (int i = tid; i < bx.n; i += nt) box[i] = (unsigned short)zrow;
-  for (int i = tid; i < NA * stride; i += nt) {
-    const int n = i / stride, g = i - n * stride;
-    ca[i] = g < n1 ? coef[((size_t)jb.k * d.nb + jb.a0 + n) * d.npw_max + g] : make_float2(0.f, 0.f);
+  for (int i = tid; i < RS * (d.npw_max + 1); i += nt) {
+    const int g = i / RS, n = i - g * RS;
+    ca[i] = (n < NA && g < n1) ? coef[((size_t)jb.k * d.nb + jb.a0 + n) * d.npw_max + g] : make_float2(0.f, 0.f);
   }
   float2* cb2 = reinterpret_cast<float2*>(cb);
   for (int i = tid; i < n2 * NKP; i += nt) {
@@ -147,10 +149,14 @@ __global__ __launch_bounds__(kGcMaxThreads) void gcorr_kernel(DevSys d, const fl
     for (int i = 0; i < 2 * P; ++i) acc[i] = 0.f;
     for (int i = 0; i < n2; ++i) {
       const int idx = box[base + lin2[i]];
-      if (__all_sync(0xffffffffu, idx == zrow)) continue;     // no lane of this warp has G2 - G in S(k)
-      float2 a[NA];
+      float2 a[(NA + 1) & ~1];
+      const float4* row = reinterpret_cast<const float4*>(ca + (size_t)idx * RS);
 #pragma unroll
-      for (int n = 0; n < NA; ++n) a[n] = ca[n * stride + idx];
+      for (int n = 0; n < (NA + 1) / 2; ++n) {
+        const float4 v = row[n];
+        a[2 * n] = make_float2(v.x, v.y);
+        a[2 * n + 1] = make_float2(v.z, v.w);
+      }
       float2 bv[NKP];
 #pragma unroll
       for (int m = 0; m < NKP / 2; ++m) {
@@ -176,7 +182,7 @@ __global__ __launch_bounds__(kGcMaxThreads) void gcorr_kernel(DevSys d, const fl
       const char4 g = d.gq[(size_t)jb.q * d.ng_max];
       if (g.x == 0 && g.y == 0 && g.z == 0 && jb.g0x == 0 && jb.g0y == 0 && jb.g0z == 0) {
         __syncwarp();
-        g0_overlaps<NV, NC, KIND>(ca, cb2, stride, n2, jb, d.ng_max);
+        g0_overlaps<NV, NC, KIND>(ca, cb2, n2, jb, d.ng_max);
       }
     }
   }
