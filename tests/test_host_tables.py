@@ -106,3 +106,36 @@ def test_symmetry_tables_bit_exact_vs_oracle(name):
     for iq in range(spec.nkpt):
         p = sy.sphere_perm(spec, iq, oibz, oqmap, ops)
         assert perm[iq, :len(p)].tolist() == p.tolist() and np.all(perm[iq, len(p):] == -1)
+
+
+def test_new_entry_points_validate_arguments(bse, cfg1):
+    """Host-side checks of the coupled, Ritz and symmetry calls: NULL or out-of-range arguments and
+    host-only plans return an error status without touching a device."""
+    import ctypes
+    lib = bse.load()
+    plan = bse.Plan([cfg1.spec], host_only=True)
+    h = plan.handle
+    # compute calls refuse a host-only plan
+    for code in (lib.bse_build_coupling(h, 0, bse.BSE_BC_INIT, None, None, 0, 0, None, 0, None, None, 0, None),
+                 lib.bse_spectrum_coupled(h, 0, None, None, None, 10, None, 0, 0.01, None, None, None, None, 0, None),
+                 lib.bse_unfold_w(h, 0, None, None, 0, 1, None)):
+        assert code == bse.BSE_ERR_ARG
+    # bse_ritz needs its pointers and 1 <= nsteps <= 4096, and a workspace of the stated size
+    assert lib.bse_ritz(None, None, 10, None, None, None, 0, None) == bse.BSE_ERR_ARG
+    dummy = ctypes.c_void_p(16)
+    assert lib.bse_ritz(dummy, dummy, 0, dummy, dummy, dummy, 1 << 30, None) == bse.BSE_ERR_ARG
+    assert lib.bse_ritz(dummy, dummy, 5000, dummy, dummy, dummy, 1 << 30, None) == bse.BSE_ERR_ARG
+    assert lib.bse_ritz(dummy, dummy, 100, dummy, dummy, dummy, 8, None) == bse.BSE_ERR_WORKSPACE
+    # workspace sizes: coupled spectrum grows with nsteps, Ritz is 6 nsteps^2 doubles
+    assert bse.bse_workspace_size(plan, 0, bse.BSE_WS_RITZ, 100) == 6 * 100 * 100 * 8
+    assert (bse.bse_workspace_size(plan, 0, bse.BSE_WS_COUPLED, 200) >
+            bse.bse_workspace_size(plan, 0, bse.BSE_WS_COUPLED, 100) > 0)
+    assert bse.bse_workspace_size(plan, 0, bse.BSE_WS_COUPLING, 0) >= 576 * 113 * 8
+    with pytest.raises(bse.BseError):
+        bse.bse_workspace_size(plan, 0, bse.BSE_WS_RITZ, 0)
+    # coupling vector count: 2 Nv Nc per upper block of the range
+    blocks = sum(len(bse.bse_pair_blocks(plan, 0, q)[0]) for q in range(3))
+    assert bse.bse_rho_cpl_count(plan, 0, 0, 3) == 2 * 9 * blocks
+    # the symmetry tables are available on a host-only plan
+    nops, ibz, qmap, perm = bse.bse_symmetry(plan, 0)
+    assert nops == 48 and len(ibz) == 8 and qmap.shape == (64, 6)
