@@ -147,8 +147,9 @@ __global__ __launch_bounds__(kGcMaxThreads) void gcorr_kernel(DevSys d, const fl
     float acc[2 * P];
 #pragma unroll
     for (int i = 0; i < 2 * P; ++i) acc[i] = 0.f;
+    int idx = n2 > 0 ? box[base + lin2[0]] : zrow;
     for (int i = 0; i < n2; ++i) {
-      const int idx = box[base + lin2[i]];
+      const int idx_next = i + 1 < n2 ? box[base + lin2[i + 1]] : zrow;   // next lookup overlaps this FMA block
       float2 a[(NA + 1) & ~1];
       const float4* row = reinterpret_cast<const float4*>(ca + (size_t)idx * RS);
 #pragma unroll
@@ -170,6 +171,7 @@ __global__ __launch_bounds__(kGcMaxThreads) void gcorr_kernel(DevSys d, const fl
         acc[2 * q] = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[2 * q]));          // conj(x) y
         acc[2 * q + 1] = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc[2 * q + 1]));
       }
+      idx = idx_next;
     }
     if (act) {
 #pragma unroll
