@@ -324,10 +324,16 @@ bse_status bse_spectrum_backward(bse_plan* plan, int s, const void* H, const voi
 /*
  * Tile-shape variants of the pair-density kernel (step A2) and their autotuner.
  *
- * Several pair-kernel variants are compiled per real-space grid (threads per CTA, z-lines per
- * chunk, maximum band products and band slabs per CTA, sphere points per thread, vv'/cc'
- * merged in one CTA or not).  A system runs the variant selected for it, by default the
- * first one valid for its grid, band counts and spheres.  No counterpart in the paper.
+ * Two routes compute the pair densities.  The plane-wave correlation kernel (variant index 64,
+ * listed first with rows = 0) sums conj(c_nk(G2 - G)) c_mk'(G2) over the sphere of k' with a
+ * shared-memory index box of the sphere of k; it is compiled for Nv, Nc in {1..3} x {1..3},
+ * (3, 4), (4, 4) and is the default where valid.  The pruned-FFT kernels (the paper's route) are
+ * compiled per real-space grid (threads per CTA, z-lines per chunk, maximum band products and
+ * band slabs per CTA, sphere points per thread, vv'/cc' merged in one CTA or not); without a
+ * valid correlation variant the first valid FFT variant is the default.  Both give the same
+ * densities to FP32 rounding; the FFT variants among themselves bit for bit.  The real-space
+ * stage (BSE_PD_REALSPACE) always runs an FFT variant of the grid and also keeps a copy of the
+ * coefficients in the pair workspace for the correlation kernel.  No counterpart in the paper.
  *
  * bse_pair_variants lists the valid variants of system s (up to cap entries of out, the
  * total in *count) and the index in use (*current).  bse_set_pair_variant selects one by its
@@ -344,7 +350,7 @@ bse_status bse_spectrum_backward(bse_plan* plan, int s, const void* H, const voi
 typedef struct {
   int index;              /* variant id (argument of bse_set_pair_variant) */
   int threads;            /* threads per CTA */
-  int rows;               /* z-lines per pipelined chunk */
+  int rows;               /* z-lines per pipelined chunk; 0: the plane-wave correlation kernel */
   int max_products;       /* band products per CTA */
   int max_bands;          /* band slabs per CTA */
   int points_per_thread;  /* sphere points accumulated per thread */
