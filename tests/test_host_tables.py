@@ -139,3 +139,25 @@ def test_new_entry_points_validate_arguments(bse, cfg1):
     # the symmetry tables are available on a host-only plan
     nops, ibz, qmap, perm = bse.bse_symmetry(plan, 0)
     assert nops == 48 and len(ibz) == 8 and qmap.shape == (64, 6)
+
+
+def test_bench_pair_work_counts_the_correlation_loop(bse, cfg1):
+    """bench.py's algorithmic work of the correlation kernel: sum over the upper blocks of
+    NG(q) |S(k')| (Nv^2 + Nc^2) complex multiply-adds, recounted from the oracle's spheres."""
+    import importlib.util
+    import os
+    spec = cfg1.spec
+    path = os.path.join(os.path.dirname(__file__), "..", "bench.py")
+    sp = importlib.util.spec_from_file_location("bench_mod", path)
+    bench = importlib.util.module_from_spec(sp)
+    sp.loader.exec_module(bench)
+    plan = bse.Plan([spec], host_only=True)
+    pw = bench.pair_work(plan, spec, plan.info(0))
+    assert pw["method"] == "correlation" and pw["variant"] == 64
+    kr = geo.mesh_offsets(spec)
+    npw = [len(geo.sphere(spec, tuple(k))) for k in kr]
+    cmac = 0
+    for ik, ik2 in geo.upper_blocks(spec):
+        iq, iqv, _ = geo.fold(spec, kr[ik], kr[ik2])
+        cmac += len(geo.sphere(spec, tuple(iqv))) * npw[ik2]
+    assert pw["cmac"] == cmac * (spec.nv ** 2 + spec.nc ** 2)
