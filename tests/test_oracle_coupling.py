@@ -133,3 +133,39 @@ def test_spectrum_odd_in_frequency(tiny):
     ep = cp.eps2_direct(spec, A, B, P, w, spec.eta)
     em = cp.eps2_direct(spec, A, B, P, -w, spec.eta)
     assert np.abs(ep + em).max() < 1e-12 * np.abs(ep).max()
+
+
+def test_half_vector_recursion_equals_full_m_lanczos(tiny):
+    """The recursion the CUDA path runs: only e-h halves x_j of the Lanczos vectors, q_j = (x_j, +-conj x_j)
+    with alternating parity, t = A x + s B conj(x), |q|_M^2 = 2 Re(x^H t), reorthogonalisation against every
+    stored vector with <q_i, w>_M = 2 Re d (same parity) or 2i Im d (other parity), d = p_i^H y, and no
+    diagonal coefficient.  In FP64 it reproduces the oracle's full 2 dim M-Lanczos coefficients."""
+    s, _, A, B, P = tiny
+    n = 40
+    a_ref, b_ref, done, s2 = cp.m_lanczos(A, B, P, n)
+    assert done == n
+    X, Pp = [], []                       # stored x_i and p_i = t_i / b_i (e-h halves)
+    b = np.zeros(n)
+    w = P.astype(np.complex128).copy()   # e-h half of s = F Pt = (P, conj P)
+    q_prev = None
+    for j in range(n):
+        sg = 1.0 if j % 2 == 0 else -1.0
+        t = A @ w + sg * (B @ np.conj(w))
+        beta2 = 2.0 * np.vdot(w, t).real
+        b[j] = np.sqrt(beta2)
+        q, p = w / b[j], t / b[j]
+        X.append(q)
+        Pp.append(p)
+        if j + 1 == n:
+            break
+        w = p - (b[j] * q_prev if q_prev is not None else 0.0)
+        for _ in range(2):
+            c = []
+            for i in range(j + 1):
+                d = np.vdot(Pp[i], w)
+                c.append(2.0 * d.real if (i - (j + 1)) % 2 == 0 else 2j * d.imag)
+            w = w - sum(ci * xi for ci, xi in zip(c, X))
+        q_prev = q
+    assert abs(b[0] ** 2 - s2) < 1e-12 * s2
+    assert np.abs(b[1:] - b_ref[1:]).max() < 1e-11 * b_ref.max()
+    assert np.abs(a_ref).max() < 1e-10 * b_ref.max()
