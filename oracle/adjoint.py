@@ -94,8 +94,9 @@ def gradients(spec, energies, delta, rho_x, factors, W, P, omega, eta, g):
     G = torch.as_tensor(grad_h(spec, H.detach().numpy(), P, omega, eta, g))
     surrogate = torch.sum(torch.conj(G) * H).real
     surrogate.backward()
-    dfac = [(f[3].grad.numpy(), f[4].grad.numpy()) for f in t_f]
-    return float(t_delta.grad), t_rx.grad.numpy(), dfac, t_W.grad.numpy(), H.detach().numpy()
+    dfac = [(f[3].grad.resolve_conj().numpy(), f[4].grad.resolve_conj().numpy()) for f in t_f]
+    return (float(t_delta.grad), t_rx.grad.resolve_conj().numpy(), dfac, t_W.grad.resolve_conj().numpy(),
+            H.detach().resolve_conj().numpy())
 
 
 def spectral_loss(spec, H, P, omega, eta, target, weight):

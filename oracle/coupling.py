@@ -101,7 +101,7 @@ def coupling_rho_block(spec, ik, ik2, gk, coef):
 
 def coupling_direct_block(spec, rvc, rcv, w) -> np.ndarray:
     """Bd block [(v,c),(v',c')] = 1/(Omega Nk) sum conj(rvc[v][c'][p]) w[p][p'] rcv[c][v'][p']."""
-    m = np.einsum("aip,pq,bjq->aibj", np.conj(rvc), w, rcv)     # [v][c'][c][v']
+    m = np.einsum("aip,pq,bjq->aibj", np.conj(rvc), w, rcv, optimize=True)     # [v][c'][c][v']
     nv, nc = rvc.shape[0], rvc.shape[1]
     return ok.norm_factor(spec) * m.transpose(0, 2, 3, 1).reshape(nv * nc, nv * nc)
 

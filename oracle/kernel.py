@@ -58,7 +58,7 @@ def exchange_kernel(spec, rho_x) -> np.ndarray:
 
 def direct_block(spec, rv, rc, w) -> np.ndarray:
     """K^d block [(v,c),(v',c')] from rho~_vv' [v][v'][p], rho~_cc' [c][c'][p], W(q) [p][p']."""
-    m = np.einsum("abp,pq,cdq->abcd", np.conj(rv), w, rc)      # [v][v'][c][c']
+    m = np.einsum("abp,pq,cdq->abcd", np.conj(rv), w, rc, optimize=True)      # [v][v'][c][c']
     nv, nc = rv.shape[0], rc.shape[0]
     return norm_factor(spec) * m.transpose(0, 2, 1, 3).reshape(nv * nc, nv * nc)
 

@@ -44,12 +44,17 @@ def rho_corr(spec, ik, ik2, bands_n, bands_m, gtargets, gk, coef) -> np.ndarray:
     lo = np.minimum(g2.min(axis=0), (g1.min(axis=0) + gt.min(axis=0))) - 1
     hi = np.maximum(g2.max(axis=0), (g1.max(axis=0) + gt.max(axis=0))) + 1
     shape = tuple(int(x) for x in (hi - lo + 1))
-    box = np.zeros((len(bands_m),) + shape, dtype=np.complex128)
-    o = g2 - lo
-    box[:, o[:, 0], o[:, 1], o[:, 2]] = c2
-    idx = g1[None, :, :] + gt[:, None, :] - lo[None, None, :]       # [G][G1][3]
-    shifted = box[:, idx[..., 0], idx[..., 1], idx[..., 2]]           # [m][G][G1]
-    return np.einsum("ni,mgi->nmg", np.conj(c1), shifted)
+    nbox = shape[0] * shape[1] * shape[2]
+    strides = np.array([shape[1] * shape[2], shape[2], 1], dtype=np.int64)
+    box = np.zeros((nbox, len(bands_m)), dtype=np.complex128)     # c_mk' on the box, bands innermost
+    box[(g2 - lo) @ strides] = c2.T
+    # c_mk'(G1 + G) for every (G1, G): the box position of G1 + G - lo is the sum of the positions of
+    # G1 - lo and of G (row-major strides of the box)
+    pos = ((g1 - lo) @ strides)[:, None] + (gt @ strides)[None, :]   # [G1][G]
+    shifted = box[pos].reshape(len(g1), len(gt) * len(bands_m))       # [G1][(G, m)]
+    # sum over G1 of conj(c_nk(G1)) c_mk'(G1 + G), as one matrix product over the G1 axis
+    r = (np.conj(c1) @ shifted).reshape(len(bands_n), len(gt), len(bands_m))     # [n][G][m]
+    return np.ascontiguousarray(r.transpose(0, 2, 1))
 
 
 def wavefunction_realspace(spec, ik, band, gk, coef) -> np.ndarray:
