@@ -27,9 +27,10 @@ Pinned by tests/test_oracle_screening.py: the (k, k+q) pair densities against br
 sums over the Born-von Karman supercell (fixes the G0 direction), chi0 Hermitian and negative
 semidefinite, eps^-1 against the Woodbury form of the inverse, the head of eps at q = 0
 against the Kramers-Kronig static limit of the independent-particle eps_2 of step A8 (fixes
-the factor 4/(Omega Nk) against the spectrum's prefactor).  The wings at q = 0 follow the
-reading above and share the weights and pair densities of the pinned parts; their own
-arrangement (conjugation of P) is parity unpinned.
+the factor 4/(Omega Nk) against the spectrum's prefactor), and the wings at q = 0 against
+the limit q -> 0 along qhat of the same matrix built from finite-q pair densities of true
+eigenstates of a model crystal Hamiltonian (for which rho_vc^{k,k+q}(0)/|q| -> conj(P_S),
+Eq. density_matrix; the synthetic random states of the workloads are not eigenstates).
 """
 from __future__ import annotations
 
