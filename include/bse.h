@@ -7,7 +7,8 @@
  *
  *   A0  plane-wave spheres, q folding, e-h pair and block tables (host)
  *   A1  u_nk(r) = sum_G c_nk(G) exp(iG.r) on the real-space grid       (Eq. pair_density)
- *   A2  rho_nm^{kk'}(G) by FFT of conj(u_nk) u_mk' pruned to the sphere (Eq. pair_density)
+ *   A2  rho_nm^{kk'}(G) on the q sphere: plane-wave correlation (default) or
+ *       pruned FFT of conj(u_nk) u_mk' (the paper's route)           (Eq. pair_density)
  *   A3  K^x = rho_x^H diag(vbar) rho_x / (Omega Nk)                   (Eq. V_eh, G = 0 dropped)
  *   A4  K^d = rho_vv'^H W(q) rho_cc' / (Omega Nk) per (k,k') block      (Eq. W_SS)
  *   A5  H = diag(e_c + Delta - e_v) + 2 K^x - K^d  (TDA, Eq. kernel)
@@ -30,6 +31,12 @@
  *    are returned by bse_status_read (which synchronises the stream).
  *  - Every function returns a bse_status; bse_last_error() gives a
  *    thread-local message for the last non-OK status.
+ *  - Non-finite inputs: each compute call first streams its caller-supplied
+ *    floating-point inputs (coef, energies, the W rows of its q range, H, A, B,
+ *    X, P, omega, dL_deps2, W_ibz) through a device scan; a NaN or an infinity
+ *    sets BSE_ERR_NONFINITE in the plan's device status word (returned by
+ *    bse_status_read), and the outputs of that call are then undefined.  The
+ *    pair densities and other library-produced intermediates are not scanned.
  *  - Systems inside one plan are addressed by index s in [0, nsys).
  */
 #ifndef BSE_H
@@ -163,8 +170,13 @@ bse_status bse_workspace_size(const bse_plan* plan, int s, int kind, long long a
 bse_status bse_rho_dir_count(const bse_plan* plan, int s, int q_begin, int q_end, long long* nvec);
 
 /*
- * A1 + A2 (+ A6).  Pair densities by batched 3D FFT (Eq. pair_density):
- *   rho_nm^{kk'}(G) = (1/N_r) sum_r conj(u_nk(r)) u_mk'(r) exp(-iG.r).
+ * A1 + A2 (+ A6).  Pair densities (Eq. pair_density):
+ *   rho_nm^{kk'}(G) = (1/N_r) sum_r conj(u_nk(r)) u_mk'(r) exp(-iG.r)
+ *                   = sum_{G2 in S(k')} conj(c_nk(G2 - G)) c_mk'(G2).
+ * Two routes give the same densities to FP32 rounding (bse_pair_variants): the
+ * plane-wave correlation kernel (second form; the default wherever its band counts
+ * are compiled) and the pruned batched 3D FFT of the products on the real-space
+ * grid (first form; the default otherwise).
  * coef     complex64 [nkpt][nb][npw_max], c_nk(G) in sphere order (zero padded).
  * energies float64  [nkpt][nb], bands ascending (valence first), Ha.
  * rho_x    complex64 [dim][ng_max]: rho_vc^{kk}(G) on the q = 0 sphere (S = (k,v,c)).
@@ -294,8 +306,10 @@ bse_status bse_spectrum_batch(bse_plan* plan, int n, const int* systems, const v
  * Limit: the scratch bse_workspace_size(BSE_WS_SPECTRUM, nsteps) reports must
  * fit in 48 MiB (roughly nsteps * dim * 16 bytes + nsteps * 16 KiB); larger
  * requests return BSE_ERR_ARG with the sizes in bse_last_error().
- * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  Every call shares
+ * Every call made outside stream capture looks up the array's device address
+ * afresh (so a cudaDeviceReset between calls is harmless); a call made while its
+ * stream is being captured reuses the address found by the last call outside
+ * capture on that device, so make one call on each device before any capture.  Every call shares
  * the one array and it keeps the last call's contents (the words that must
  * start at zero are cleared by each call): calls that overlap on the GPU race.
  */

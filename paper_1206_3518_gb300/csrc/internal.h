@@ -116,6 +116,10 @@ size_t kernel_ws_bytes(const DevSys& d, long long qchunk);
 int launch_gemm_wr(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long vbase, long long max_rows,
                    const void* W, void* X, int side_c, void* stream);
 
+// Streams n elements of elem_bytes (4: float / complex64 parts, 8: double) through a NaN/Inf check;
+// a hit sets BSE_ERR_NONFINITE in *status.  n <= 0 launches nothing.
+int launch_nonfinite_scan(const void* p, long long n, int elem_bytes, int* status, void* stream);
+
 size_t spectrum_static_capacity();
 int set_wait_limit(unsigned long long ns);
 int launch_spectrum_static(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw,

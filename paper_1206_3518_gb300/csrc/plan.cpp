@@ -445,6 +445,11 @@ bse_status check_device_plan(const bse_plan* plan, int s) {
   return BSE_OK;
 }
 
+// Non-finite scan of one caller input (see launch_nonfinite_scan); NULL or empty inputs are skipped.
+bse_status scan_input(const bse_plan* plan, const void* p, long long n, int elem_bytes, void* stream) {
+  return cuda_check(launch_nonfinite_scan(p, n, elem_bytes, plan->d_status, stream), "input scan");
+}
+
 bse_status create(const bse_system* sys, int nsys, bse_plan** out, bool device) {
   if (!sys || nsys < 1 || !out) return set_error(BSE_ERR_ARG, "need sys, nsys >= 1 and out");
   *out = nullptr;
@@ -603,6 +608,7 @@ bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags, const void*
   if (!pair_supported(d)) return set_error(BSE_ERR_UNSUPPORTED, "no pair-FFT kernel compiled for this grid/sphere");
   if (flags & BSE_PD_REALSPACE) {
     if (!coef) return set_error(BSE_ERR_ARG, "coef is NULL");
+    if ((st = scan_input(plan, coef, 2LL * d.nkpt * d.nb * d.npw_max, 4, stream)) != BSE_OK) return st;
     if ((st = cuda_check(launch_realspace(d, coef, ws, stream), "realspace")) != BSE_OK) return st;
   }
   if (flags & BSE_PD_EXCHANGE) {
@@ -610,6 +616,7 @@ bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags, const void*
     if (rho_x && (st = cuda_check(launch_pair_exchange(d, ws, rho_x, plan->d_status, stream), "pair exchange")) != BSE_OK) return st;
     if (P) {
       if (!coef || !energies) return set_error(BSE_ERR_ARG, "dipole needs coef and energies");
+      if ((st = scan_input(plan, energies, (long long)d.nkpt * d.nb, 8, stream)) != BSE_OK) return st;
       if ((st = cuda_check(launch_dipole(d, coef, energies, sp.sys.gap_floor, P, stream), "dipole")) != BSE_OK)
         return st;
     }
@@ -730,6 +737,7 @@ bse_status bse_build_kernel(bse_plan* plan, int s, unsigned flags, const void* r
   if (prec != BSE_PREC_FP32 && prec != BSE_PREC_BF16X3) return set_error(BSE_ERR_ARG, "unknown precision");
   if (flags & BSE_BK_INIT) {
     if (!rho_x || !energies) return set_error(BSE_ERR_ARG, "init needs rho_x and energies");
+    if ((st = scan_input(plan, energies, (long long)d.nkpt * d.nb, 8, stream)) != BSE_OK) return st;
     if ((st = cuda_check(launch_kernel_init(d, rho_x, energies, delta, H, stream), "kernel init")) != BSE_OK)
       return st;
   }
@@ -739,6 +747,10 @@ bse_status bse_build_kernel(bse_plan* plan, int s, unsigned flags, const void* r
     if (!ws || ws_bytes < kernel_ws_bytes(d, q_end - q_begin))
       return set_error(BSE_ERR_WORKSPACE, "kernel workspace too small");
     const SysPlan& sp = plan->sys[s];
+    const long long ng2 = (long long)d.ng_max * d.ng_max;
+    if ((st = scan_input(plan, (const char*)W + (size_t)q_begin * ng2 * 8, 2 * (q_end - q_begin) * ng2, 4, stream)) !=
+        BSE_OK)
+      return st;
     const long long b0 = sp.qblk_off[q_begin], nb = sp.qblk_off[q_end] - b0, vb = sp.qvec_off[q_begin];
     const long long w = (d.nc * d.nc < d.nv * d.nv) ? d.nc * d.nc : d.nv * d.nv;
     long long max_rows = 0;
@@ -759,6 +771,9 @@ bse_status bse_apply_H(bse_plan* plan, int s, const void* H, const void* X, void
   bse_status st = check_device_plan(plan, s);
   if (st != BSE_OK) return st;
   if (!H || !X || !Y || nvec < 1) return set_error(BSE_ERR_ARG, "apply_H needs H, X, Y and nvec >= 1");
+  const DevSys& dd = plan->sys[s].d;
+  if ((st = scan_input(plan, H, 2LL * dd.dim * dd.dim, 4, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, X, 2LL * nvec * dd.dim, 8, stream)) != BSE_OK) return st;
   return cuda_check(launch_apply_h(plan->sys[s].d, H, X, Y, nvec, stream), "apply_H");
 }
 
@@ -772,6 +787,9 @@ bse_status bse_spectrum(bse_plan* plan, int s, const void* H, const void* P, int
     return set_error(BSE_ERR_ARG, "spectrum needs H, P, omega, eps2, ab, steps_done, nsteps >= 1, eta > 0");
   if (nsteps > d.dim) return set_error(BSE_ERR_ARG, "nsteps > dim");
   if (!ws || ws_bytes < spectrum_ws_bytes(d, nsteps)) return set_error(BSE_ERR_WORKSPACE, "spectrum workspace too small");
+  if ((st = scan_input(plan, H, 2LL * d.dim * d.dim, 4, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, P, 2LL * d.dim, 8, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, omega, nw, 8, stream)) != BSE_OK) return st;
   const int e = launch_spectrum(d, H, P, nsteps, omega, nw, eta, eps2, ab, steps_done, ws, plan->d_status, stream);
   if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "cooperative launch not possible on this device");
   return cuda_check(e, "spectrum");
@@ -797,6 +815,16 @@ bse_status bse_spectrum_batch(bse_plan* plan, int n, const int* systems, const v
     if (ws_bytes[i] < spectrum_ws_bytes(d, nsteps)) return set_error(BSE_ERR_WORKSPACE, "batch workspace too small");
     jobs[i] = HayJob{&d, H[i], P[i], eps2[i], ab[i], steps_done[i], ws[i]};
   }
+  for (int i = 0; i < n; ++i) {
+    const DevSys& d = plan->sys[systems[i]].d;
+    bse_status st = scan_input(plan, H[i], 2LL * d.dim * d.dim, 4, stream);
+    if (st == BSE_OK) st = scan_input(plan, P[i], 2LL * d.dim, 8, stream);
+    if (st != BSE_OK) return st;
+  }
+  {
+    bse_status st = scan_input(plan, omega, nw, 8, stream);
+    if (st != BSE_OK) return st;
+  }
   const int e = run_haydock_batch(jobs.data(), n, nsteps, omega, nw, eta, plan->d_status, stream);
   if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "cooperative launch not possible on this device");
   if (e == -2) return set_error(BSE_ERR_ARG, "more batched systems than SMs");
@@ -816,6 +844,9 @@ bse_status bse_spectrum_static(bse_plan* plan, int s, const void* H, const void*
     return set_error(BSE_ERR_ARG, "scratch of " + std::to_string(need) + " bytes exceeds the library's static " +
                                       std::to_string(spectrum_static_capacity()) +
                                       "-byte spectrum scratch; use bse_spectrum with a caller workspace");
+  if ((st = scan_input(plan, H, 2LL * d.dim * d.dim, 4, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, P, 2LL * d.dim, 8, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, omega, nw, 8, stream)) != BSE_OK) return st;
   const int e = launch_spectrum_static(d, H, P, nsteps, omega, nw, eta, eps2, ab, steps_done, plan->d_status, stream);
   if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "cooperative launch not possible on this device");
   return cuda_check(e, "spectrum (static scratch)");
@@ -835,6 +866,11 @@ bse_status bse_spectrum_backward(bse_plan* plan, int s, const void* H, const voi
   if ((dL_drho_x && !rho_x) || ((dL_drho_dir || dL_dW) && (!rho_dir || !W)))
     return set_error(BSE_ERR_ARG, "chained gradients need their forward inputs");
   if (!ws || ws_bytes < backward_ws_bytes(d, nsteps)) return set_error(BSE_ERR_WORKSPACE, "backward workspace too small");
+  if ((st = scan_input(plan, H, 2LL * d.dim * d.dim, 4, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, P, 2LL * d.dim, 8, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, omega, nw, 8, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, dL_deps2, nw, 8, stream)) != BSE_OK) return st;
+  if (W && (st = scan_input(plan, W, 2LL * d.nq * d.ng_max * d.ng_max, 4, stream)) != BSE_OK) return st;
   const SysPlan& sp = plan->sys[s];
   const int e = launch_backward(d, sp.qblk_off.data(), sp.qvec_off.data(), H, P, nsteps, omega, nw, eta, dL_deps2,
                                 rho_x, rho_dir, W, dL_ddelta, dL_dH, dL_drho_x, dL_drho_dir, dL_dW, ws,
@@ -856,6 +892,8 @@ bse_status bse_screening(bse_plan* plan, int s, void* rho_chi, const double* ene
     return set_error(BSE_ERR_ARG, "bad screening arguments");
   if (q_begin == 0 && !P) return set_error(BSE_ERR_ARG, "q = 0 needs the dipole P");
   if (!ws || ws_bytes < screen_ws_bytes(d, q_end - q_begin)) return set_error(BSE_ERR_WORKSPACE, "workspace too small");
+  if ((st = scan_input(plan, energies, (long long)d.nkpt * d.nb, 8, stream)) != BSE_OK) return st;
+  if (q_begin == 0 && (st = scan_input(plan, P, 2LL * d.dim, 8, stream)) != BSE_OK) return st;
   return cuda_check(launch_screening(d, rho_chi, energies, P, q_begin, q_end, iterations, W, residual, ws,
                                      sp.sys.gap_floor, stream),
                     "screening");
@@ -893,6 +931,10 @@ bse_status bse_build_coupling(bse_plan* plan, int s, unsigned flags, const void*
       return set_error(BSE_ERR_ARG, "direct stage needs rho_cpl, W and a q range");
     if (!ws || ws_bytes < coupling_ws_bytes(d, q_end - q_begin))
       return set_error(BSE_ERR_WORKSPACE, "coupling workspace too small");
+    const long long ng2 = (long long)d.ng_max * d.ng_max;
+    if ((st = scan_input(plan, (const char*)W + (size_t)q_begin * ng2 * 8, 2 * (q_end - q_begin) * ng2, 4, stream)) !=
+        BSE_OK)
+      return st;
     const long long w = (long long)d.nv * d.nc;
     const long long nb = sp.qblk_off[q_end] - sp.qblk_off[q_begin], vb = 2 * w * sp.qblk_off[q_begin];
     long long max_rows = 0;
@@ -918,6 +960,10 @@ bse_status bse_spectrum_coupled(bse_plan* plan, int s, const void* A, const void
     return set_error(BSE_ERR_ARG, "coupled spectrum needs A, Bm, P, omega, eps2, b, steps_done, nsteps >= 1, eta > 0");
   if (nsteps > 2 * d.dim) return set_error(BSE_ERR_ARG, "nsteps > 2 dim");
   if (!ws || ws_bytes < coupled_ws_bytes(d, nsteps)) return set_error(BSE_ERR_WORKSPACE, "coupled workspace too small");
+  if ((st = scan_input(plan, A, 2LL * d.dim * d.dim, 4, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, Bm, 2LL * d.dim * d.dim, 4, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, P, 2LL * d.dim, 8, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, omega, nw, 8, stream)) != BSE_OK) return st;
   const int e = launch_spectrum_coupled(d, A, Bm, P, nsteps, omega, nw, eta, eps2, b, steps_done, ws, plan->d_status,
                                         stream);
   if (e == -2) return set_error(BSE_ERR_UNSUPPORTED, "coupled spectrum is built for dim <= 65536");
@@ -942,6 +988,7 @@ bse_status bse_unfold_w(bse_plan* plan, int s, const void* W_ibz, void* W, int q
   if (st != BSE_OK) return st;
   const DevSys& d = plan->sys[s].d;
   if (!W_ibz || !W || q_begin < 0 || q_end > d.nq || q_begin >= q_end) return set_error(BSE_ERR_ARG, "bad unfold arguments");
+  if ((st = scan_input(plan, W_ibz, 2LL * d.nibz * d.ng_max * d.ng_max, 4, stream)) != BSE_OK) return st;
   return cuda_check(launch_unfold_w(d, W_ibz, W, q_begin, q_end, stream), "unfold W");
 }
 
