@@ -844,9 +844,11 @@ int launch_spectrum(const DevSys& d, const void* H, const void* P, int nsteps, c
 // memory themselves.  The scratch is one file-scope device array of fixed size;
 // every device that loads this library holds it until the process exits.  Host
 // code may not pass the array's name to a kernel (in host code it is only a
-// stand-in for the symbol), so its device address is looked up once per device
-// with cudaGetSymbolAddress and cached.  All calls share the array: calls that
-// overlap on the GPU race on it.
+// stand-in for the symbol), so its device address is looked up with
+// cudaGetSymbolAddress on every call made outside stream capture (a module
+// reloaded after cudaDeviceReset gets a fresh address) and cached per device for
+// calls made while the stream is being captured.  All calls share the array:
+// calls that overlap on the GPU race on it.
 namespace {
 constexpr size_t kStaticScratchBytes = size_t(48) << 20;
 static __device__ __align__(256) unsigned char g_spectrum_scratch[kStaticScratchBytes];
@@ -863,10 +865,13 @@ int launch_spectrum_static(const DevSys& d, const void* H, const void* P, int ns
   int e = (int)cudaGetDevice(&dev);
   if (e) return e;
   if (dev < 0 || dev >= kMaxDevices) return (int)cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  e = (int)cudaStreamIsCapturing((cudaStream_t)stream, &capture);
+  if (e) return e;
   void* ws = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    if (capture == cudaStreamCaptureStatusNone || !g_scratch_addr[dev]) {
       void* p = nullptr;
       e = (int)cudaGetSymbolAddress(&p, g_spectrum_scratch);
       if (e) return e;
