@@ -638,7 +638,11 @@ def run_stage(args):
     from paper_1206_3518_gb300 import bse
     from paper_1206_3518_gb300.pipeline import Forward
 
-    spec, s = make_inputs(args.config)
+    from synth import config_spec, generate
+    spec = config_spec(args.config)
+    if args.nk:
+        spec = spec.replace(nk=(args.nk,) * 3)
+    s = generate(spec, wdtype=np.complex64)
     plan = bse.Plan([spec])
     qchunk = args.qchunk or (16 if args.only in ("pair", "contract") else 32)
     F = Forward(plan, 0, nsteps=spec.nsteps, nw=spec.nw, qchunk=qchunk)
@@ -946,6 +950,8 @@ def main():
                     help="profiling aid: run one stage (pair: realspace + a q chunk of pair densities; "
                          "spectrum: Haydock on an H built once before the loop)")
     ap.add_argument("--qchunk", type=int, default=0, help="q points per direct-term chunk (0 = automatic)")
+    ap.add_argument("--nk", type=int, default=0,
+                    help="profiling aid for --only: the workload's per-block shape on an nk^3 k mesh")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -126,8 +126,12 @@ def test_spectrum_matches_oracle_haydock(bse, cfg1, cfg1_oracle):
     a32, b32, _, _ = osp.haydock(cfg1_oracle["H"].astype(np.complex64).astype(np.complex128), cfg1_oracle["P"], 100)
     fa = np.abs(a32 - a).max() / np.abs(a).max()
     fb = np.abs(b32 - b).max() / np.abs(b).max()
-    assert np.abs(ab[:100] - a).max() < max(1e-5, 10.0 * fa) * np.abs(a).max()
-    assert np.abs(ab[100:] - b).max() < max(1e-5, 10.0 * fb) * np.abs(b).max()
+    ea = np.abs(ab[:100] - a).max() / np.abs(a).max()
+    eb = np.abs(ab[100:] - b).max() / np.abs(b).max()
+    print(f"Haydock coefficients vs the oracle: a {ea:.2e} (FP32-storage floor {fa:.2e}), "
+          f"b {eb:.2e} (floor {fb:.2e}); eps_2 {np.abs(eps - ref).max() / ref.max():.2e}")
+    assert ea < max(1e-5, 10.0 * fa)
+    assert eb < max(1e-5, 10.0 * fb)
 
 
 def test_spectrum_full_krylov_equals_dense_eig(bse, cfg1, cfg1_oracle):
