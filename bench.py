@@ -644,6 +644,8 @@ def run_stage(args):
         spec = spec.replace(nk=(args.nk,) * 3)
     s = generate(spec, wdtype=np.complex64)
     plan = bse.Plan([spec])
+    if args.variant >= 0:
+        bse.bse_set_pair_variant(plan, 0, args.variant)
     qchunk = args.qchunk or (16 if args.only in ("pair", "contract") else 32)
     F = Forward(plan, 0, nsteps=spec.nsteps, nw=spec.nw, qchunk=qchunk)
     dev = torch.device("cuda")
@@ -950,6 +952,7 @@ def main():
                     help="profiling aid: run one stage (pair: realspace + a q chunk of pair densities; "
                          "spectrum: Haydock on an H built once before the loop)")
     ap.add_argument("--qchunk", type=int, default=0, help="q points per direct-term chunk (0 = automatic)")
+    ap.add_argument("--variant", type=int, default=-1, help="profiling aid for --only pair: pair-kernel variant index")
     ap.add_argument("--nk", type=int, default=0,
                     help="profiling aid for --only: the workload's per-block shape on an nk^3 k mesh")
     args = ap.parse_args()

@@ -13,7 +13,7 @@ import os
 from . import bse
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "tune_cache.json")
-_FIELDS = ("threads", "rows", "max_products", "max_bands", "points_per_thread", "merged")
+_FIELDS = ("index", "threads", "rows", "max_products", "max_bands", "points_per_thread", "merged")
 
 
 def shape_key(plan, s, device_name: str) -> str:
@@ -46,7 +46,7 @@ def tune(plan, s, forward, q_begin=0, q_end=None, reps=3, cache_path=DEFAULT_CAC
     hit = cache.get(key)
     if hit is not None and not force:
         for v in variants:
-            if all(v[f] == hit["variant"][f] for f in _FIELDS):
+            if all(v[f] == hit["variant"].get(f) for f in _FIELDS):
                 bse.bse_set_pair_variant(plan, s, v["index"])
                 return {"variant": v, "ms": {}, "cached": True}
     if q_end is None:

@@ -96,7 +96,7 @@ __device__ __noinline__ void g0_overlaps(const float2* ca, const float2* cb2, in
   }
 }
 
-template <int NV, int NC, int KIND>
+template <int NV, int NC, int KIND, int PF>
 __global__ __launch_bounds__(kGcMaxThreads) void gcorr_kernel(DevSys d, const float2* __restrict__ coef,
                                                               float2* __restrict__ out, int mode, int q0, int nqc,
                                                               long long vbase, Box bx) {
@@ -147,31 +147,71 @@ __global__ __launch_bounds__(kGcMaxThreads) void gcorr_kernel(DevSys d, const fl
     float acc[2 * P];
 #pragma unroll
     for (int i = 0; i < 2 * P; ++i) acc[i] = 0.f;
-    int idx = n2 > 0 ? box[base + lin2[0]] : zrow;
-    for (int i = 0; i < n2; ++i) {
-      const int idx_next = i + 1 < n2 ? box[base + lin2[i + 1]] : zrow;   // next lookup overlaps this FMA block
-      float2 a[(NA + 1) & ~1];
-      const float4* row = reinterpret_cast<const float4*>(ca + (size_t)idx * RS);
+    constexpr int NAP = (NA + 1) & ~1;
+    if (PF) {
+      // Software pipeline: the k bands of G2 index i + 1 (box lookup, then the gathered row) are loaded
+      // while the products of index i run, so the two dependent shared-memory loads overlap the FMA block.
+      const float4* ca4 = reinterpret_cast<const float4*>(ca);
+      float4 a4[NAP / 2];
+      {
+        const int idx0 = n2 > 0 ? box[base + lin2[0]] : zrow;
 #pragma unroll
-      for (int n = 0; n < (NA + 1) / 2; ++n) {
-        const float4 v = row[n];
-        a[2 * n] = make_float2(v.x, v.y);
-        a[2 * n + 1] = make_float2(v.z, v.w);
+        for (int n = 0; n < NAP / 2; ++n) a4[n] = ca4[idx0 * (RS / 2) + n];
       }
-      float2 bv[NKP];
+      for (int i = 0; i < n2; ++i) {
+        const int idx_next = i + 1 < n2 ? box[base + lin2[i + 1]] : zrow;
+        float4 an4[NAP / 2];
 #pragma unroll
-      for (int m = 0; m < NKP / 2; ++m) {
-        const float4 v = cb[(size_t)i * (NKP / 2) + m];
-        bv[2 * m] = make_float2(v.x, v.y);
-        bv[2 * m + 1] = make_float2(v.z, v.w);
-      }
+        for (int n = 0; n < NAP / 2; ++n) an4[n] = ca4[idx_next * (RS / 2) + n];
+        float2 a[NAP];
 #pragma unroll
-      for (int q = 0; q < P; ++q) {
-        const float2 x = a[S::a(q)], y = bv[S::b(q)];
-        acc[2 * q] = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[2 * q]));          // conj(x) y
-        acc[2 * q + 1] = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc[2 * q + 1]));
+        for (int n = 0; n < NAP / 2; ++n) {
+          a[2 * n] = make_float2(a4[n].x, a4[n].y);
+          a[2 * n + 1] = make_float2(a4[n].z, a4[n].w);
+        }
+        float2 bv[NKP];
+#pragma unroll
+        for (int m = 0; m < NKP / 2; ++m) {
+          const float4 v = cb[i * (NKP / 2) + m];
+          bv[2 * m] = make_float2(v.x, v.y);
+          bv[2 * m + 1] = make_float2(v.z, v.w);
+        }
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const float2 x = a[S::a(q)], y = bv[S::b(q)];
+          acc[2 * q] = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[2 * q]));          // conj(x) y
+          acc[2 * q + 1] = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc[2 * q + 1]));
+        }
+#pragma unroll
+        for (int n = 0; n < NAP / 2; ++n) a4[n] = an4[n];
       }
-      idx = idx_next;
+    } else {
+      int idx = n2 > 0 ? box[base + lin2[0]] : zrow;
+      for (int i = 0; i < n2; ++i) {
+        const int idx_next = i + 1 < n2 ? box[base + lin2[i + 1]] : zrow;   // next lookup overlaps this FMA block
+        float2 a[NAP];
+        const float4* row = reinterpret_cast<const float4*>(ca + (size_t)idx * RS);
+#pragma unroll
+        for (int n = 0; n < NAP / 2; ++n) {
+          const float4 v = row[n];
+          a[2 * n] = make_float2(v.x, v.y);
+          a[2 * n + 1] = make_float2(v.z, v.w);
+        }
+        float2 bv[NKP];
+#pragma unroll
+        for (int m = 0; m < NKP / 2; ++m) {
+          const float4 v = cb[(size_t)i * (NKP / 2) + m];
+          bv[2 * m] = make_float2(v.x, v.y);
+          bv[2 * m + 1] = make_float2(v.z, v.w);
+        }
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const float2 x = a[S::a(q)], y = bv[S::b(q)];
+          acc[2 * q] = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[2 * q]));          // conj(x) y
+          acc[2 * q + 1] = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc[2 * q + 1]));
+        }
+        idx = idx_next;
+      }
     }
     if (act) {
 #pragma unroll
@@ -192,17 +232,20 @@ __global__ __launch_bounds__(kGcMaxThreads) void gcorr_kernel(DevSys d, const fl
 
 typedef void (*GcFn)(DevSys, const float2*, float2*, int, int, int, long long, Box);
 
+// fn[kind][pf]: pf = 1 is the software-pipelined gather
 struct GcEntry {
   int nv, nc;
-  GcFn fn[3];
+  GcFn fn[3][2];
   size_t (*smem[3])(const DevSys&, const Box&);
 };
 
 #define BSE_GC(NV, NC)                                                                                   \
   GcEntry {                                                                                              \
-    NV, NC, {gcorr_kernel<NV, NC, 0>, gcorr_kernel<NV, NC, 1>, gcorr_kernel<NV, NC, 2>}, {                \
-      smem_bytes<NV, NC, 0>, smem_bytes<NV, NC, 1>, smem_bytes<NV, NC, 2>                                 \
-    }                                                                                                    \
+    NV, NC,                                                                                              \
+        {{gcorr_kernel<NV, NC, 0, 0>, gcorr_kernel<NV, NC, 0, 1>},                                       \
+         {gcorr_kernel<NV, NC, 1, 0>, gcorr_kernel<NV, NC, 1, 1>},                                       \
+         {gcorr_kernel<NV, NC, 2, 0>, gcorr_kernel<NV, NC, 2, 1>}},                                      \
+        {smem_bytes<NV, NC, 0>, smem_bytes<NV, NC, 1>, smem_bytes<NV, NC, 2>}                            \
   }
 
 // band counts compiled: the fcc workloads (3v3c, 3v4c, 4v4c, the 2v2c test cell) and every
@@ -248,18 +291,20 @@ int gcorr_valid(const DevSys& d) {
 
 int gcorr_threads(const DevSys& d) { return threads_of(d); }
 
-// kind 0: exchange / screening sets, 1: direct set, 2: coupling set; cells = CTAs of the launch.
+// kind 0: exchange / screening sets, 1: direct set, 2: coupling set; cells = CTAs of the launch;
+// pf = 1: the software-pipelined gather.
 int launch_gcorr(const DevSys& d, const void* coef, void* out, int kind, int mode, int q0, int nqc, long long vbase,
-                 long long cells, void* stream) {
+                 long long cells, int pf, void* stream) {
   const GcEntry* e = find(d);
   if (!e || kind < 0 || kind > 2) return (int)cudaErrorInvalidValue;
   if (cells <= 0) return 0;
   if (cells >= (1LL << 31)) return (int)cudaErrorInvalidValue;
   const Box bx = box_of(d);
   const size_t sm = e->smem[kind](d, bx);
-  int err = (int)cudaFuncSetAttribute((const void*)e->fn[kind], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const GcFn fn = e->fn[kind][pf ? 1 : 0];
+  int err = (int)cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (err) return err;
-  e->fn[kind]<<<(unsigned)cells, threads_of(d), sm, (cudaStream_t)stream>>>(d, (const float2*)coef, (float2*)out,
+  fn<<<(unsigned)cells, threads_of(d), sm, (cudaStream_t)stream>>>(d, (const float2*)coef, (float2*)out,
                                                                           mode, q0, nqc, vbase, bx);
   return (int)cudaGetLastError();
 }

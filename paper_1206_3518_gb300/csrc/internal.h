@@ -80,7 +80,7 @@ size_t pair_ws_bytes(const DevSys& d);
 int gcorr_valid(const DevSys& d);
 int gcorr_threads(const DevSys& d);
 int launch_gcorr(const DevSys& d, const void* coef, void* out, int kind, int mode, int q0, int nqc, long long vbase,
-                 long long cells, void* stream);
+                 long long cells, int pf, void* stream);
 // Pair-kernel variants compiled for this system: writes up to cap (index, threads, rows, pmax, bmax, ppt,
 // merged) septets, returns the number valid; pair_variant_current returns the index pick() uses.
 int pair_variants(const DevSys& d, int* out, int cap);

@@ -430,10 +430,15 @@ const Variant* pick(const DevSys& d) {
 
 // The plane-wave correlation kernel (gcorr.cu) is variant kGcorrIndex; it is the default wherever it
 // is compiled for the system's band counts, and the FFT variants stay selectable.
-constexpr int kGcorrIndex = 64;
+// Variant kGcorrPfIndex is the same kernel with the gather of the next G2 row software-pipelined.
+constexpr int kGcorrIndex = 64, kGcorrPfIndex = 65;
+constexpr int kGcorrDefaultPf = 0;
 bool use_gcorr(const DevSys& d) {
   if (!gcorr_valid(d)) return false;
-  return d.pair_variant == -1 || d.pair_variant == kGcorrIndex;
+  return d.pair_variant == -1 || d.pair_variant == kGcorrIndex || d.pair_variant == kGcorrPfIndex;
+}
+int gcorr_pf(const DevSys& d) {
+  return d.pair_variant == kGcorrPfIndex ? 1 : d.pair_variant == kGcorrIndex ? 0 : kGcorrDefaultPf;
 }
 
 // Coefficients c_nk(G) are kept after u_nk(r) in the pair workspace (the correlation kernel reads them).
@@ -476,17 +481,20 @@ size_t pair_ws_bytes(const DevSys& d) { return u_bytes(d) + (size_t)d.nkpt * d.n
 int pair_variants(const DevSys& d, int* out, int cap) {
   int n = 0;
   if (gcorr_valid(d)) {                      // rows = 0 marks the plane-wave correlation kernel
-    if (out && n < cap) {
-      int* o = out + 7 * n;
-      o[0] = kGcorrIndex;
-      o[1] = gcorr_threads(d);
-      o[2] = 0;
-      o[3] = 2 * d.nv * d.nc > d.nv * d.nv + d.nc * d.nc ? 2 * d.nv * d.nc : d.nv * d.nv + d.nc * d.nc;
-      o[4] = 2 * d.nb;
-      o[5] = 1;
-      o[6] = 1;
+    const int order[2] = {kGcorrDefaultPf ? kGcorrPfIndex : kGcorrIndex, kGcorrDefaultPf ? kGcorrIndex : kGcorrPfIndex};
+    for (int idx : order) {
+      if (out && n < cap) {
+        int* o = out + 7 * n;
+        o[0] = idx;
+        o[1] = gcorr_threads(d);
+        o[2] = 0;
+        o[3] = 2 * d.nv * d.nc > d.nv * d.nv + d.nc * d.nc ? 2 * d.nv * d.nc : d.nv * d.nv + d.nc * d.nc;
+        o[4] = 2 * d.nb;
+        o[5] = 1;
+        o[6] = 1;
+      }
+      ++n;
     }
-    ++n;
   }
   for (int i = 0; i < kNumVariants; ++i) {
     const Variant& v = kVariants[i];
@@ -507,7 +515,7 @@ int pair_variants(const DevSys& d, int* out, int cap) {
 }
 
 int pair_variant_current(const DevSys& d) {
-  if (use_gcorr(d)) return kGcorrIndex;
+  if (use_gcorr(d)) return gcorr_pf(d) ? kGcorrPfIndex : kGcorrIndex;
   const Variant* v = pick(d);
   return v ? (int)(v - kVariants) : -1;
 }
@@ -523,7 +531,7 @@ int launch_realspace(const DevSys& d, const void* coef, void* u, void* stream) {
 }
 
 int launch_pair_exchange(const DevSys& d, const void* u, void* rho_x, int* status, void* stream) {
-  if (use_gcorr(d)) return launch_gcorr(d, coef_copy(d, u), rho_x, 0, 0, 0, 0, 0, d.nkpt, stream);
+  if (use_gcorr(d)) return launch_gcorr(d, coef_copy(d, u), rho_x, 0, 0, 0, 0, 0, d.nkpt, gcorr_pf(d), stream);
   const Variant* v = pick(d);
   if (!v) return (int)cudaErrorInvalidValue;
   const size_t sm = v->pair_smem(d.ng_max);
@@ -543,7 +551,7 @@ int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, int q_begi
                        int* status, void* stream) {
   if (use_gcorr(d))
     return launch_gcorr(d, coef_copy(d, u), rho_dir, 1, 1, q_begin, q_end - q_begin, vbase,
-                        job_cells(d, q_end - q_begin, true), stream);
+                        job_cells(d, q_end - q_begin, true), gcorr_pf(d), stream);
   const Variant* v = pick(d);
   if (!v) return (int)cudaErrorInvalidValue;
   const size_t sm = v->pair_smem(d.ng_max);
@@ -565,7 +573,7 @@ int launch_pair_coupling(const DevSys& d, const void* u, void* rho_cpl, int q_be
                          int* status, void* stream) {
   if (use_gcorr(d))
     return launch_gcorr(d, coef_copy(d, u), rho_cpl, 2, 5, q_begin, q_end - q_begin, vbase,
-                        job_cells(d, q_end - q_begin, true), stream);
+                        job_cells(d, q_end - q_begin, true), gcorr_pf(d), stream);
   const Variant* v = pick(d);
   if (!v) return (int)cudaErrorInvalidValue;
   const size_t sm = v->pair_smem(d.ng_max);
@@ -585,7 +593,7 @@ int launch_pair_coupling(const DevSys& d, const void* u, void* rho_cpl, int q_be
 int launch_pair_chi0(const DevSys& d, const void* u, void* rho, int q_begin, int q_end, int* status, void* stream) {
   if (use_gcorr(d))
     return launch_gcorr(d, coef_copy(d, u), rho, 0, 4, q_begin, q_end - q_begin, 0,
-                        (long long)(q_end - q_begin) * d.nkpt, stream);
+                        (long long)(q_end - q_begin) * d.nkpt, gcorr_pf(d), stream);
   const Variant* v = pick(d);
   if (!v) return (int)cudaErrorInvalidValue;
   const size_t sm = v->pair_smem(d.ng_max);

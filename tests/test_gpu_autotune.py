@@ -50,7 +50,7 @@ def test_variants_bit_identical_and_match_oracle(bse, spec):
     coef, en = _dev(s.coef, torch.complex64), _dev(s.energies, torch.float64)
     assert any(v["rows"] == 0 for v in variants) and variants[0]["rows"] == 0    # correlation kernel first
     g = op.exchange_rho(spec, s.gk, s.coef)
-    ref, outs = None, []
+    ref, cref, outs = None, None, []
     for v in variants:
         bse.bse_set_pair_variant(plan, 0, v["index"])
         assert bse.bse_pair_variants(plan, 0)[1] == v["index"]
@@ -66,6 +66,11 @@ def test_variants_bit_identical_and_match_oracle(bse, spec):
         rx = got[0][:, :g.shape[1]]
         assert np.abs(rx - g).max() / np.abs(g).max() < 1e-5, v        # exchange densities vs the oracle
         if v["rows"] == 0:
+            # the correlation kernels (plain and pipelined gather) run the same sums in the same order
+            if cref is None:
+                cref = got
+            else:
+                assert np.array_equal(got[0], cref[0]) and np.array_equal(got[1], cref[1]), v
             continue
         if ref is None:
             ref = got
@@ -86,7 +91,7 @@ def test_autotune_picks_fastest_and_caches(bse, tmp_path):
     s = generate(spec, wdtype=np.complex64)
     plan = bse.Plan([spec])
     variants, _ = bse.bse_pair_variants(plan, 0)
-    assert len(variants) == 4            # the correlation kernel and three FFT tile shapes
+    assert len(variants) == 5            # the correlation kernel (two gather schedules) and three FFT tile shapes
     F = Forward(plan, 0, nsteps=10, nw=50, qchunk=32)
     bse.bse_pair_densities(plan, 0, bse.BSE_PD_REALSPACE, _dev(s.coef, torch.complex64),
                            _dev(s.energies, torch.float64), None, None, None, 0, 0, F.ws_pair)
@@ -94,7 +99,7 @@ def test_autotune_picks_fastest_and_caches(bse, tmp_path):
     r = autotune.tune(plan, 0, F, reps=2, cache_path=cache)
     assert not r["cached"]
     ms = r["ms"]
-    assert len(ms) == 4 and all(t > 0 for t in ms.values())
+    assert len(ms) == 5 and all(t > 0 for t in ms.values())
     assert r["variant"]["index"] == int(min(ms, key=ms.get))
     assert bse.bse_pair_variants(plan, 0)[1] == r["variant"]["index"]
     stored = json.load(open(cache))
