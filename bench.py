@@ -689,10 +689,15 @@ def run_stage(args):
 
 
 
-# DRAM bytes (read + write) per direct-pair-density launch of the correlation kernel, measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) and valid only for the kernel sources with this SHA-1
-# (gcorr.cu + pairjob.cuh) and the named workload and q chunk.
-GCORR_TRAFFIC = {}
+# DRAM bytes (read + write) per upper block of the correlation kernel's direct set, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, one launch) of the fcc 12x12x12 4v4c block shape (Ecut 12,
+# 48^3 grid) on a 6x6x6 k mesh: 23,436 blocks (all 216 q) in one launch, 4.5 GB on the device, 159.7 MB read
+# and 2944.9 MB written.  A full launch of the workload processes nblocks / q_chunks blocks of the same shape
+# and the bytes grow with the blocks (the densities are written once, the coefficients are read from L2), so
+# the traffic per launch is this figure times the launch's blocks.  Valid only for the sources with this
+# SHA-1 (gcorr.cu + pairjob.cuh) and that block shape.
+GCORR_TRAFFIC = {"sha1": "98a94e850b910092ba14723d028b70a6dc285429", "bytes_per_block": 132469.9,
+                 "shape": ("fcc", 4, 4, 12.0)}
 
 
 def _gcorr_sources_sha1():
@@ -733,9 +738,9 @@ def stage_rooflines(st, spec, inf, peaks, src, nchunks, pw, prec):
     ms = st["pair_direct"]
     if pw["method"] == "correlation":
         flops = 8.0 * pw["cmac"]
-        key = f"{spec.name}/q_chunk_launches_{nchunks}"
-        tr = GCORR_TRAFFIC.get(key)
-        traffic = (tr["bytes_per_launch"] if tr and tr["sha1"] == _gcorr_sources_sha1() else None)
+        same = (GCORR_TRAFFIC["shape"] == (spec.lattice, spec.nv, spec.nc, spec.ecut)
+                and GCORR_TRAFFIC["sha1"] == _gcorr_sources_sha1())
+        traffic = GCORR_TRAFFIC["bytes_per_block"] * nb / nchunks if same else None
         out["pair_direct"] = {
             "bound": "alu", "kernel": "gcorr_kernel", "achieved": flops / (ms / 1e3) / 1e12, "peak": fp32,
             "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / fp32, "launches_per_step": nchunks,
