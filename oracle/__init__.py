@@ -7,7 +7,8 @@ k.p dipole (Eq. density_matrix), the spectrum from the spectral representation
 of the irreducible response (Eq. epsilon_chi_bar, Appendix A), its gradient, the static
 RPA screening from the independent-particle response (Eqs. chi0_GG, epsilon_-1), the problem
 with e-h / h-e coupling beyond the Tamm-Dancoff approximation (Appendix A), and the q-point
-symmetry reduction of W (Sec. III A).
+symmetry reduction of W (Sec. III A), and the macroscopic dielectric function from TDDFT with
+local fields (Sec. II A-B).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA path
@@ -18,4 +19,4 @@ Parity status per function is stated in each module header; every function is
 pinned by ``tests/test_oracle_*.py`` against closed forms, brute force,
 invariants or textbook limits.
 """
-from . import geometry, pair, kernel, spectrum, adjoint, screening, coupling, symmetry  # noqa: F401
+from . import geometry, pair, kernel, spectrum, adjoint, screening, coupling, symmetry, tddft  # noqa: F401
