@@ -379,7 +379,7 @@ def run_secondary(args, dev, rank, world, peaks):
     from paper_1206_3518_gb300.pipeline import Forward
 
     out = {}
-    if world == 1 and not (args.no_screening and args.no_coupled and args.no_symmetry):
+    if world == 1 and not (args.no_screening and args.no_coupled and args.no_symmetry and args.no_tddft):
         spec, s = make_inputs(SECONDARY)
         plan = bse.Plan([spec])
         inf = plan.info(0)
@@ -398,11 +398,79 @@ def run_secondary(args, dev, rank, world, peaks):
             out["symmetry"] = run_symmetry(plan, inf, W, dev)
         if not args.no_coupled:
             out["coupled"] = run_coupled(args, dev, spec, W, om, F, peaks)
+        if not args.no_tddft:
+            out["tddft"] = run_tddft(args, dev, spec, s, en, F, peaks)
         del F, coef, en, W, om
         torch.cuda.empty_cache()
     if not args.no_batch:
         out["batch"] = run_batch(args, dev, rank, world)
     return out
+
+
+def run_tddft(args, dev, spec, s, en, F, peaks):
+    """Macroscopic dielectric function from TDDFT with local fields on the workload's frequency grid: the
+    optical-limit Adler-Wiser response chi~0(w) for every frequency, the ALDA kernel and the Dyson solve with
+    RPA and ALDA kernels (eps_M = 1/[eps^-1]_00).  CUDA-event times; returns the JSON summary."""
+    import torch
+    from paper_1206_3518_gb300 import bse
+    plan = F.plan
+    inf = plan.info(0)
+    ng, dim, nw = inf["ng0"], inf["dim"], spec.nw
+    omega = torch.as_tensor(s.omega, device=dev)
+    bse.bse_pair_densities(plan, 0, bse.BSE_PD_REALSPACE | bse.BSE_PD_EXCHANGE, torch.as_tensor(
+        s.coef.astype("complex64"), device=dev), en, F.rho_x, F.P, None, 0, 0, F.ws_pair)
+    chi = torch.empty(nw, ng, ng, dtype=torch.complex64, device=dev)
+    ws = torch.empty(bse.bse_workspace_size(plan, 0, bse.BSE_WS_CHI0) // 8 + 1, dtype=torch.complex64, device=dev)
+    Fx = torch.empty(ng, ng, dtype=torch.complex64, device=dev)
+    wsa = torch.empty(bse.bse_workspace_size(plan, 0, bse.BSE_WS_ALDA) // 8 + 1, dtype=torch.complex64, device=dev)
+    wse = torch.empty(bse.bse_workspace_size(plan, 0, bse.BSE_WS_EPSM, nw) // 8 + 1, dtype=torch.complex64,
+                      device=dev)
+    e_rpa = torch.empty(nw, dtype=torch.complex128, device=dev)
+    e_alda = torch.empty(nw, dtype=torch.complex128, device=dev)
+    eta = spec.eta
+
+    def once(ev=None):
+        marks = []
+
+        def mark():
+            if ev is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record()
+                marks.append(e)
+        mark()
+        bse.bse_chi0_optical(plan, 0, F.rho_x, F.P, en, spec.delta, omega, eta, chi, ws)
+        mark()
+        bse.bse_xc_kernel_alda(plan, 0, F.ws_pair, Fx, wsa)
+        mark()
+        bse.bse_epsilon_macro(plan, 0, chi, None, e_rpa, wse)
+        mark()
+        bse.bse_epsilon_macro(plan, 0, chi, Fx, e_alda, wse)
+        mark()
+        if ev is not None:
+            ev.append(marks)
+
+    once()
+    torch.cuda.synchronize()
+    bse.bse_status_read(plan)
+    evs = []
+    for _ in range(2):
+        once(evs)
+    torch.cuda.synchronize()
+    bse.bse_status_read(plan)
+    t = [statistics.mean(m[i].elapsed_time(m[i + 1]) for m in evs) for i in range(4)]
+    flops = 2.0 * 8.0 * nw * ng * ng * dim            # two weighted Gram terms, 8 flops per complex MAC
+    ach = flops / (t[0] / 1e3) / 1e12
+    fp32 = _fp32_peak(peaks)
+    er = e_rpa.cpu().numpy()
+    ea = e_alda.cpu().numpy()
+    i = int(abs(s.omega).argmin())
+    return {"workload": f"{spec.name}, q -> 0 sphere of {ng} G, {dim} transitions, {nw} w, eta {eta:.4f} Ha",
+            "chi0_ms": t[0], "alda_kernel_ms": t[1], "eps_m_rpa_ms": t[2], "eps_m_alda_ms": t[3],
+            "chi0_roofline": {"bound": "alu", "kernel": "chi0_kernel", "achieved": ach, "peak": fp32,
+                              "unit": "TFLOP/s", "frac": ach / fp32,
+                              "work": "2 x 8 FP32 flops per complex MAC of nw ng0^2 dim"},
+            "eps_m_static_rpa": float(er[i].real), "eps_m_static_alda": float(ea[i].real),
+            "static_frequency_ha": float(s.omega[i])}
 
 
 def run_symmetry(plan, inf, W, dev):
@@ -953,6 +1021,7 @@ def main():
     ap.add_argument("--no-screening", action="store_true", help="skip the static RPA screening measurement")
     ap.add_argument("--no-coupled", action="store_true", help="skip the BSE with e-h / h-e coupling")
     ap.add_argument("--no-symmetry", action="store_true", help="skip the q-point symmetry measurement")
+    ap.add_argument("--no-tddft", action="store_true", help="skip the TDDFT macroscopic dielectric function")
     ap.add_argument("--only", default="all", choices=["all", "pair", "spectrum", "contract"],
                     help="profiling aid: run one stage (pair: realspace + a q chunk of pair densities; "
                          "spectrum: Haydock on an H built once before the loop)")

@@ -73,7 +73,10 @@ typedef enum {
   BSE_WS_SCREEN = 4,    /* bse_screening: dielectric matrices of one q chunk (arg = chunk) */
   BSE_WS_COUPLING = 5,  /* bse_build_coupling: W.rho_cv' of one q chunk (arg = chunk; 0 = INIT only) */
   BSE_WS_COUPLED = 6,   /* bse_spectrum_coupled: basis, vectors, partial sums (arg = nsteps) */
-  BSE_WS_RITZ = 7       /* bse_ritz: per-Ritz-value scratch (arg = nsteps <= 4096; plan/system unused) */
+  BSE_WS_RITZ = 7,      /* bse_ritz: per-Ritz-value scratch (arg = nsteps <= 4096; plan/system unused) */
+  BSE_WS_CHI0 = 8,      /* bse_chi0_optical: pair vectors of the optical response */
+  BSE_WS_ALDA = 9,      /* bse_xc_kernel_alda: f_xc(r) and the transform passes */
+  BSE_WS_EPSM = 10      /* bse_epsilon_macro: augmented Dyson systems (arg = nw) */
 } bse_ws_kind;
 
 /* Stage flags for bse_pair_densities and bse_build_kernel. */
@@ -456,6 +459,43 @@ bse_status bse_build_coupling(bse_plan* plan, int s, unsigned flags, const void*
 bse_status bse_spectrum_coupled(bse_plan* plan, int s, const void* A, const void* Bm, const void* P, int nsteps,
                                 const double* omega, int nw, double eta, double* eps2, double* b, int* steps_done,
                                 void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Macroscopic dielectric function from TDDFT with local fields (Sec. II A-B: Eqs. epsilon_M,
+ * epsilon_-1, Dyson_GG, chi0_GG) in the optical limit q -> 0 along qhat, on the q = 0 sphere
+ * (ng0 vectors G).  Bulk (3D Coulomb) systems with a q = 0 sphere symmetric under G -> -G.
+ *
+ * bse_chi0_optical: the symmetrised Adler-Wiser response chi~0 = v^1/2 chi0 v^1/2 for nw frequencies,
+ *   chi~0_GG'(w) = 2/(Omega Nk) sum_S [ a_S(G) conj a_S(G') / (w - de_S + i eta)
+ *                                      - abar_S(G) conj abar_S(G') / (w + de_S + i eta) ],
+ *   a_S(G) = v^1/2(G) rho_vc^{kk}(G), abar_S(G) = v^1/2(G) conj(rho_vc^{kk}(-G)) for G != 0 (v^1/2(G) =
+ *   sqrt(4 pi)/|G|), a_S(0) = sqrt(4 pi) conj(P_S), abar_S(0) = -sqrt(4 pi) P_S (the k.p limit of
+ *   Eq. density_matrix), de_S = e_c + delta - e_v (delta = 0: the band energies as given).
+ *   rho_x    complex64 [dim][ng_max] and P complex128 [dim] from bse_pair_densities (EXCHANGE).
+ *   energies float64 [Nk][Nb];  omega float64 [nw] (Ha);  eta > 0 (Ha).
+ *   chi0     complex64 [nw][ng0][ng0] row-major (row G, column G').
+ *   ws       bse_workspace_size(BSE_WS_CHI0) bytes.
+ *   FP32 products and sums (64 x 64 output tiles per frequency).
+ * bse_xc_kernel_alda: F = v^-1/2 f_xc v^-1/2 of the adiabatic local-density kernel,
+ *   F_GG' = |G| f_xc(G - G') |G'| / (4 pi),  f_xc(G) = (1/N_r) sum_r f_xc(r) exp(-iG.r),
+ *   f_xc(r) = d^2(n eps_xc)/dn^2 at n(r) = 2/(Omega Nk) sum_{k,v} |u_vk(r)|^2 (floor 1e-6 bohr^-3), eps_xc
+ *   Slater exchange + Perdew-Zunger (Ceperley-Alder) correlation, spin-unpolarised; row and column
+ *   G = 0 are zero (q -> 0).  pair_ws: the pair workspace after bse_pair_densities(BSE_PD_REALSPACE)
+ *   (it holds u_nk(r) on the grid).  F complex64 [ng0][ng0].  ws: bse_workspace_size(BSE_WS_ALDA).
+ *   Errors: BSE_ERR_UNSUPPORTED when the grid cannot hold the G - G' box of the sphere.
+ * bse_epsilon_macro: for every frequency, eps^-1 = I + (I - chi~0 (I + F))^-1 chi~0 and
+ *   eps_M(w) = 1/[eps^-1]_00 (F = NULL: the RPA, K = v).  One Dyson system per frequency, solved by
+ *   Gaussian elimination with partial pivoting in FP32 (one CTA per frequency); eps_m complex128 [nw].
+ *   ws: bse_workspace_size(BSE_WS_EPSM, nw).  Errors: BSE_ERR_UNSUPPORTED for ng0 > 4096.
+ * Inputs are scanned for NaN/Inf (BSE_ERR_NONFINITE through bse_status_read).  No device-side waits.
+ */
+bse_status bse_chi0_optical(bse_plan* plan, int s, const void* rho_x, const void* P, const double* energies,
+                            double delta, const double* omega, int nw, double eta, void* chi0, void* ws,
+                            size_t ws_bytes, void* stream);
+bse_status bse_xc_kernel_alda(bse_plan* plan, int s, const void* pair_ws, size_t pair_ws_bytes, void* F, void* ws,
+                              size_t ws_bytes, void* stream);
+bse_status bse_epsilon_macro(bse_plan* plan, int s, const void* chi0, const void* F, int nw, void* eps_m, void* ws,
+                             size_t ws_bytes, void* stream);
 
 /*
  * Failure injection: limit (ns) of every grid-barrier wait of the spectrum kernels (steps A7,

@@ -22,6 +22,7 @@ BSE_COULOMB_3D, BSE_COULOMB_SLAB = 0, 1
 BSE_PREC_FP32, BSE_PREC_BF16X3 = 0, 1
 BSE_WS_PAIR, BSE_WS_KERNEL, BSE_WS_SPECTRUM, BSE_WS_BACKWARD, BSE_WS_SCREEN = 0, 1, 2, 3, 4
 BSE_WS_COUPLING, BSE_WS_COUPLED, BSE_WS_RITZ = 5, 6, 7
+BSE_WS_CHI0, BSE_WS_ALDA, BSE_WS_EPSM = 8, 9, 10
 BSE_PD_REALSPACE, BSE_PD_EXCHANGE, BSE_PD_DIRECT, BSE_PD_CHI0, BSE_PD_COUPLING = 1, 2, 4, 8, 16
 BSE_BK_INIT, BSE_BK_DIRECT, BSE_BK_MIRROR = 1, 2, 4
 BSE_BC_INIT, BSE_BC_DIRECT, BSE_BC_MIRROR = 1, 2, 4
@@ -32,6 +33,7 @@ EXPORTED = [
     "bse_build_kernel", "bse_apply_H", "bse_spectrum", "bse_spectrum_static", "bse_spectrum_batch", "bse_spectrum_backward", "bse_status_read",
     "bse_pair_variants", "bse_set_pair_variant", "bse_autotune_pair", "bse_set_wait_limit", "bse_screening",
     "bse_rho_cpl_count", "bse_build_coupling", "bse_spectrum_coupled", "bse_ritz", "bse_symmetry", "bse_unfold_w",
+    "bse_chi0_optical", "bse_xc_kernel_alda", "bse_epsilon_macro",
 ]
 
 
@@ -105,6 +107,9 @@ def load():
     lib.bse_ritz.argtypes = [vp, vp, i, vp, vp, vp, sz, vp]
     lib.bse_symmetry.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), vp, vp, vp]
     lib.bse_unfold_w.argtypes = [vp, i, vp, vp, i, i, vp]
+    lib.bse_chi0_optical.argtypes = [vp, i, vp, vp, vp, d, vp, i, d, vp, vp, sz, vp]
+    lib.bse_xc_kernel_alda.argtypes = [vp, i, vp, sz, vp, vp, sz, vp]
+    lib.bse_epsilon_macro.argtypes = [vp, i, vp, vp, i, vp, vp, sz, vp]
     for name in EXPORTED:
         if name != "bse_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -352,3 +357,21 @@ def bse_symmetry(plan, s):
 def bse_unfold_w(plan, s, W_ibz, W, q_begin, q_end):
     """W on the q range from W on the irreducible points (Sec. III A)."""
     _check(load().bse_unfold_w(plan.handle, s, _ptr(W_ibz), _ptr(W), q_begin, q_end, _stream()))
+
+
+def bse_chi0_optical(plan, s, rho_x, P, energies, delta, omega, eta, chi0, ws):
+    """Symmetrised Adler-Wiser response chi~0(w) [nw][ng0][ng0] in the optical limit (TDDFT, Sec. II B)."""
+    _check(load().bse_chi0_optical(plan.handle, s, _ptr(rho_x), _ptr(P), _ptr(energies), float(delta), _ptr(omega),
+                                   omega.numel(), float(eta), _ptr(chi0), _ptr(ws), _nbytes(ws), _stream()))
+
+
+def bse_xc_kernel_alda(plan, s, pair_ws, F, ws):
+    """F = v^-1/2 f_xc v^-1/2 [ng0][ng0] of the adiabatic local-density kernel (density from the pair workspace)."""
+    _check(load().bse_xc_kernel_alda(plan.handle, s, _ptr(pair_ws), _nbytes(pair_ws), _ptr(F), _ptr(ws), _nbytes(ws),
+                                     _stream()))
+
+
+def bse_epsilon_macro(plan, s, chi0, F, eps_m, ws):
+    """eps_M(w) = 1/[eps^-1]_00 from the Dyson equation with K = v (F None) or v + f_xc (complex128 [nw])."""
+    _check(load().bse_epsilon_macro(plan.handle, s, _ptr(chi0), _ptr(F), eps_m.numel(), _ptr(eps_m), _ptr(ws),
+                                    _nbytes(ws), _stream()))

@@ -120,6 +120,16 @@ int launch_gemm_wr(const DevSys& d, const void* rho_dir, int q_begin, int q_end,
 // a hit sets BSE_ERR_NONFINITE in *status.  n <= 0 launches nothing.
 int launch_nonfinite_scan(const void* p, long long n, int elem_bytes, int* status, void* stream);
 
+// Macroscopic dielectric function from TDDFT with local fields (tddft.cu).
+size_t chi0_ws_bytes(const DevSys& d);
+int launch_chi0_optical(const DevSys& d, const void* rho_x, const void* P, const double* energies, double delta,
+                        const double* omega, int nw, double eta, void* chi0, void* ws, void* stream);
+size_t alda_ws_bytes(const DevSys& d);
+int launch_alda_kernel(const DevSys& d, const void* pair_ws, const int* m, void* F, void* ws, void* stream);
+size_t epsm_ws_bytes(const DevSys& d, long long nw);
+int launch_epsilon_macro(const DevSys& d, const void* chi0, const void* F, int nw, void* eps_m, void* ws,
+                         void* stream);
+
 size_t spectrum_static_capacity();
 int set_wait_limit(unsigned long long ns);
 int launch_spectrum_static(const DevSys& d, const void* H, const void* P, int nsteps, const double* omega, int nw,

@@ -582,6 +582,16 @@ bse_status bse_workspace_size(const bse_plan* plan, int s, int kind, long long a
       if (arg < 1 || arg > 4096) return set_error(BSE_ERR_ARG, "nsteps outside [1, 4096]");
       *bytes = ritz_ws_bytes(arg);
       return BSE_OK;
+    case BSE_WS_CHI0:
+      *bytes = chi0_ws_bytes(d);
+      return BSE_OK;
+    case BSE_WS_ALDA:
+      *bytes = alda_ws_bytes(d);
+      return BSE_OK;
+    case BSE_WS_EPSM:
+      if (arg < 1) return set_error(BSE_ERR_ARG, "nw must be >= 1");
+      *bytes = epsm_ws_bytes(d, arg);
+      return BSE_OK;
   }
   return set_error(BSE_ERR_ARG, "unknown workspace kind");
 }
@@ -968,6 +978,57 @@ bse_status bse_spectrum_coupled(bse_plan* plan, int s, const void* A, const void
                                         stream);
   if (e == -2) return set_error(BSE_ERR_UNSUPPORTED, "coupled spectrum is built for dim <= 65536");
   return cuda_check(e, "coupled spectrum");
+}
+
+bse_status bse_chi0_optical(bse_plan* plan, int s, const void* rho_x, const void* P, const double* energies,
+                            double delta, const double* omega, int nw, double eta, void* chi0, void* ws,
+                            size_t ws_bytes, void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const SysPlan& sp = plan->sys[s];
+  const DevSys& d = sp.d;
+  if (sp.sys.coulomb != BSE_COULOMB_3D) return set_error(BSE_ERR_UNSUPPORTED, "the optical response is built for bulk systems");
+  if (!sp.gminus0_complete) return set_error(BSE_ERR_UNSUPPORTED, "q = 0 sphere is not symmetric under G -> -G");
+  if (!rho_x || !P || !energies || !omega || !chi0 || nw < 1 || !(eta > 0.0))
+    return set_error(BSE_ERR_ARG, "chi0 needs rho_x, P, energies, omega, chi0, nw >= 1 and eta > 0");
+  if (!ws || ws_bytes < chi0_ws_bytes(d)) return set_error(BSE_ERR_WORKSPACE, "chi0 workspace too small");
+  if ((st = scan_input(plan, P, 2LL * d.dim, 8, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, energies, (long long)d.nkpt * d.nb, 8, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, omega, nw, 8, stream)) != BSE_OK) return st;
+  return cuda_check(launch_chi0_optical(d, rho_x, P, energies, delta, omega, nw, eta, chi0, ws, stream), "chi0");
+}
+
+bse_status bse_xc_kernel_alda(bse_plan* plan, int s, const void* pair_ws, size_t pair_bytes, void* F, void* ws,
+                              size_t ws_bytes, void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const SysPlan& sp = plan->sys[s];
+  const DevSys& d = sp.d;
+  if (sp.sys.coulomb != BSE_COULOMB_3D) return set_error(BSE_ERR_UNSUPPORTED, "the ALDA kernel is built for bulk systems");
+  if (!pair_ws || !F) return set_error(BSE_ERR_ARG, "ALDA needs the pair workspace and F");
+  if (pair_bytes < pair_ws_bytes(d)) return set_error(BSE_ERR_WORKSPACE, "pair workspace too small");
+  if (!ws || ws_bytes < alda_ws_bytes(d)) return set_error(BSE_ERR_WORKSPACE, "ALDA workspace too small");
+  int m[3] = {0, 0, 0};
+  const std::vector<int32_t>& g0 = sp.gq[0];
+  for (size_t t = 0; t + 2 < g0.size(); t += 3)
+    for (int i = 0; i < 3; ++i) m[i] = std::max(m[i], 2 * std::abs(g0[t + i]));
+  const int n[3] = {d.n1, d.n2, d.n3};
+  for (int i = 0; i < 3; ++i)
+    if (2 * m[i] + 1 > n[i]) return set_error(BSE_ERR_UNSUPPORTED, "grid too small for the G - G' box of the q = 0 sphere");
+  return cuda_check(launch_alda_kernel(d, pair_ws, m, F, ws, stream), "ALDA kernel");
+}
+
+bse_status bse_epsilon_macro(bse_plan* plan, int s, const void* chi0, const void* F, int nw, void* eps_m, void* ws,
+                             size_t ws_bytes, void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const DevSys& d = plan->sys[s].d;
+  if (!chi0 || !eps_m || nw < 1) return set_error(BSE_ERR_ARG, "eps_M needs chi0, eps_m and nw >= 1");
+  if (d.ng0 > 4096) return set_error(BSE_ERR_UNSUPPORTED, "q = 0 sphere larger than 4096");
+  if (!ws || ws_bytes < epsm_ws_bytes(d, nw)) return set_error(BSE_ERR_WORKSPACE, "eps_M workspace too small");
+  if ((st = scan_input(plan, chi0, 2LL * nw * d.ng0 * d.ng0, 4, stream)) != BSE_OK) return st;
+  if (F && (st = scan_input(plan, F, 2LL * d.ng0 * d.ng0, 4, stream)) != BSE_OK) return st;
+  return cuda_check(launch_epsilon_macro(d, chi0, F, nw, eps_m, ws, stream), "eps_M");
 }
 
 bse_status bse_symmetry(const bse_plan* plan, int s, int* nops, int* nibz, int32_t* ibz, int32_t* qmap,
