@@ -76,7 +76,8 @@ typedef enum {
   BSE_WS_RITZ = 7,      /* bse_ritz: per-Ritz-value scratch (arg = nsteps <= 4096; plan/system unused) */
   BSE_WS_CHI0 = 8,      /* bse_chi0_optical: pair vectors of the optical response */
   BSE_WS_ALDA = 9,      /* bse_xc_kernel_alda: f_xc(r) and the transform passes */
-  BSE_WS_EPSM = 10      /* bse_epsilon_macro: augmented Dyson systems (arg = nw) */
+  BSE_WS_EPSM = 10,     /* bse_epsilon_macro: augmented Dyson systems (arg = nw) */
+  BSE_WS_STATES = 11    /* bse_exciton_states: Krylov basis, tridiagonal eigenvectors (arg = n) */
 } bse_ws_kind;
 
 /* Stage flags for bse_pair_densities and bse_build_kernel. */
@@ -281,6 +282,24 @@ bse_status bse_unfold_w(bse_plan* plan, int s, const void* W_ibz, void* W, int q
  */
 bse_status bse_ritz(const double* ab, const int* steps_done, int nsteps, double* theta, double* weight, void* ws,
                     size_t ws_bytes, void* stream);
+
+/*
+ * Exciton states (Eq. bse_eig): eigenpairs H A_l = E_l A_l.  A Lanczos tridiagonalisation of Krylov
+ * dimension n from the start vector X0 (complex128 [dim], any norm): the recursion of bse_spectrum
+ * (FP32 products with H, Gram-Schmidt twice against the whole stored basis, FP64 coefficients), then
+ * the eigenvalues of the tridiagonal T by bisection and its eigenvectors y_l by inverse iteration
+ * (FP64), and A_l = sum_j y_l(j) v_j.  With n = dim and an X0 that overlaps every eigenvector (e.g.
+ * a random vector) the pairs are all eigenpairs of H; with n < dim they are the Ritz pairs of the
+ * Krylov space (extreme and isolated states first).  Eigenvalues that coincide to rounding appear
+ * once; a breakdown (an invariant Krylov space) ends the recursion early, with steps_done < n.
+ * theta float64 [n] ascending (entries >= steps_done zero);  A complex64 [n][dim], row l the unit
+ * eigenvector of theta_l (optional, may be NULL);  ab float64 [2 n] and steps_done int32 [1] as in
+ * bse_spectrum.  ws: bse_workspace_size(BSE_WS_STATES, n) bytes (about n dim 16 B + 7 n^2 8 B).
+ * One persistent cooperative launch (bounded grid-barrier waits, BSE_ERR_TIMEOUT through
+ * bse_status_read) and two kernels.  Errors: BSE_ERR_ARG (n outside [1, dim]), BSE_ERR_WORKSPACE.
+ */
+bse_status bse_exciton_states(bse_plan* plan, int s, const void* H, const void* X0, int n, double* theta, void* A,
+                              double* ab, int* steps_done, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * A7 + A8 for a batch of n <= 24 systems of one plan in ONE persistent cooperative

@@ -22,7 +22,7 @@ BSE_COULOMB_3D, BSE_COULOMB_SLAB = 0, 1
 BSE_PREC_FP32, BSE_PREC_BF16X3 = 0, 1
 BSE_WS_PAIR, BSE_WS_KERNEL, BSE_WS_SPECTRUM, BSE_WS_BACKWARD, BSE_WS_SCREEN = 0, 1, 2, 3, 4
 BSE_WS_COUPLING, BSE_WS_COUPLED, BSE_WS_RITZ = 5, 6, 7
-BSE_WS_CHI0, BSE_WS_ALDA, BSE_WS_EPSM = 8, 9, 10
+BSE_WS_CHI0, BSE_WS_ALDA, BSE_WS_EPSM, BSE_WS_STATES = 8, 9, 10, 11
 BSE_PD_REALSPACE, BSE_PD_EXCHANGE, BSE_PD_DIRECT, BSE_PD_CHI0, BSE_PD_COUPLING = 1, 2, 4, 8, 16
 BSE_BK_INIT, BSE_BK_DIRECT, BSE_BK_MIRROR = 1, 2, 4
 BSE_BC_INIT, BSE_BC_DIRECT, BSE_BC_MIRROR = 1, 2, 4
@@ -33,7 +33,7 @@ EXPORTED = [
     "bse_build_kernel", "bse_apply_H", "bse_spectrum", "bse_spectrum_static", "bse_spectrum_batch", "bse_spectrum_backward", "bse_status_read",
     "bse_pair_variants", "bse_set_pair_variant", "bse_autotune_pair", "bse_set_wait_limit", "bse_screening",
     "bse_rho_cpl_count", "bse_build_coupling", "bse_spectrum_coupled", "bse_ritz", "bse_symmetry", "bse_unfold_w",
-    "bse_chi0_optical", "bse_xc_kernel_alda", "bse_epsilon_macro",
+    "bse_chi0_optical", "bse_xc_kernel_alda", "bse_epsilon_macro", "bse_exciton_states",
 ]
 
 
@@ -110,6 +110,7 @@ def load():
     lib.bse_chi0_optical.argtypes = [vp, i, vp, vp, vp, d, vp, i, d, vp, vp, sz, vp]
     lib.bse_xc_kernel_alda.argtypes = [vp, i, vp, sz, vp, vp, sz, vp]
     lib.bse_epsilon_macro.argtypes = [vp, i, vp, vp, i, vp, vp, sz, vp]
+    lib.bse_exciton_states.argtypes = [vp, i, vp, vp, i, vp, vp, vp, vp, vp, sz, vp]
     for name in EXPORTED:
         if name != "bse_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -375,3 +376,10 @@ def bse_epsilon_macro(plan, s, chi0, F, eps_m, ws):
     """eps_M(w) = 1/[eps^-1]_00 from the Dyson equation with K = v (F None) or v + f_xc (complex128 [nw])."""
     _check(load().bse_epsilon_macro(plan.handle, s, _ptr(chi0), _ptr(F), eps_m.numel(), _ptr(eps_m), _ptr(ws),
                                     _nbytes(ws), _stream()))
+
+
+def bse_exciton_states(plan, s, H, X0, n, theta, A, ab, steps_done, ws):
+    """Eigenpairs of H (Eq. bse_eig) from a Lanczos tridiagonalisation of Krylov dimension n started at X0:
+    theta [n] ascending, A [n][dim] unit eigenvectors (A may be None)."""
+    _check(load().bse_exciton_states(plan.handle, s, _ptr(H), _ptr(X0), int(n), _ptr(theta), _ptr(A), _ptr(ab),
+                                     _ptr(steps_done), _ptr(ws), _nbytes(ws), _stream()))

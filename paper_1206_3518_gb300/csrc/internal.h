@@ -109,6 +109,11 @@ size_t ritz_ws_bytes(long long nsteps);
 int launch_unfold_w(const DevSys& d, const void* W_ibz, void* W, int q_begin, int q_end, void* stream);
 int launch_ritz(const double* ab, const int* steps_done, int nsteps, double* theta, double* weight, void* ws,
                 void* stream);
+int launch_ritz_vectors(const double* ab, const int* steps_done, int nsteps, double* theta, double* weight, void* ws,
+                        double* vecs, void* stream);
+size_t states_ws_bytes(const DevSys& d, long long n);
+int launch_exciton_states(const DevSys& d, const void* H, const void* X0, int n, double* theta, void* A, double* ab,
+                          int* steps_done, void* ws, int* status, void* stream);
 int launch_spectrum_coupled(const DevSys& d, const void* A, const void* Bm, const void* P, int nsteps,
                             const double* omega, int nw, double eta, double* eps2, double* b, int* steps_done,
                             void* ws, int* status, void* stream);

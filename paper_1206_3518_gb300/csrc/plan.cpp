@@ -592,6 +592,10 @@ bse_status bse_workspace_size(const bse_plan* plan, int s, int kind, long long a
       if (arg < 1) return set_error(BSE_ERR_ARG, "nw must be >= 1");
       *bytes = epsm_ws_bytes(d, arg);
       return BSE_OK;
+    case BSE_WS_STATES:
+      if (arg < 1 || arg > d.dim) return set_error(BSE_ERR_ARG, "n outside [1, dim]");
+      *bytes = states_ws_bytes(d, arg);
+      return BSE_OK;
   }
   return set_error(BSE_ERR_ARG, "unknown workspace kind");
 }
@@ -1029,6 +1033,21 @@ bse_status bse_epsilon_macro(bse_plan* plan, int s, const void* chi0, const void
   if ((st = scan_input(plan, chi0, 2LL * nw * d.ng0 * d.ng0, 4, stream)) != BSE_OK) return st;
   if (F && (st = scan_input(plan, F, 2LL * d.ng0 * d.ng0, 4, stream)) != BSE_OK) return st;
   return cuda_check(launch_epsilon_macro(d, chi0, F, nw, eps_m, ws, stream), "eps_M");
+}
+
+bse_status bse_exciton_states(bse_plan* plan, int s, const void* H, const void* X0, int n, double* theta, void* A,
+                              double* ab, int* steps_done, void* ws, size_t ws_bytes, void* stream) {
+  bse_status st = check_device_plan(plan, s);
+  if (st != BSE_OK) return st;
+  const DevSys& d = plan->sys[s].d;
+  if (!H || !X0 || !theta || !ab || !steps_done || n < 1 || n > d.dim)
+    return set_error(BSE_ERR_ARG, "exciton states need H, X0, theta, ab, steps_done and 1 <= n <= dim");
+  if (!ws || ws_bytes < states_ws_bytes(d, n)) return set_error(BSE_ERR_WORKSPACE, "exciton-state workspace too small");
+  if ((st = scan_input(plan, H, 2LL * d.dim * d.dim, 4, stream)) != BSE_OK) return st;
+  if ((st = scan_input(plan, X0, 2LL * d.dim, 8, stream)) != BSE_OK) return st;
+  const int e = launch_exciton_states(d, H, X0, n, theta, A, ab, steps_done, ws, plan->d_status, stream);
+  if (e == -1) return set_error(BSE_ERR_UNSUPPORTED, "cooperative launch not possible on this device");
+  return cuda_check(e, "exciton states");
 }
 
 bse_status bse_symmetry(const bse_plan* plan, int s, int* nops, int* nibz, int32_t* ibz, int32_t* qmap,

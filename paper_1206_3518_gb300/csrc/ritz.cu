@@ -49,17 +49,22 @@ __device__ void lu_solve(const double* d, const double* u, const double* u2, con
   for (int j = n - 3; j >= 0; --j) r[j] = (r[j] - u[j] * r[j + 1] - u2[j] * r[j + 2]) / d[j];
 }
 
+// vecs (optional) [nsteps][nsteps]: row i receives the normalised eigenvector of T for theta_i (zero
+// past the recursion's length and for rows i >= steps done).
 __global__ __launch_bounds__(kRitzThreads) void ritz_kernel(const double* __restrict__ ab,
                                                            const int* __restrict__ steps_done, int nsteps,
                                                            double* __restrict__ theta, double* __restrict__ weight,
-                                                           double* __restrict__ ws) {
+                                                           double* __restrict__ ws, double* __restrict__ vecs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsteps) return;
   int n = *steps_done;
   n = n < nsteps ? n : nsteps;
+  double* vrow = vecs ? vecs + (size_t)i * nsteps : nullptr;
   if (i >= n || n < 1) {
     theta[i] = 0.0;
     weight[i] = 0.0;
+    if (vrow)
+      for (int j = 0; j < nsteps; ++j) vrow[j] = 0.0;
     return;
   }
   const double* a = ab;
@@ -67,6 +72,8 @@ __global__ __launch_bounds__(kRitzThreads) void ritz_kernel(const double* __rest
   if (n == 1) {
     theta[i] = a[0];
     weight[i] = 1.0;
+    if (vrow)
+      for (int j = 0; j < nsteps; ++j) vrow[j] = j == 0 ? 1.0 : 0.0;
     return;
   }
   double lo = DBL_MAX, hi = -DBL_MAX, scale = 0.0;
@@ -130,6 +137,10 @@ __global__ __launch_bounds__(kRitzThreads) void ritz_kernel(const double* __rest
   double s2 = 0.0;
   for (int j = 0; j < n; ++j) s2 += x[j] * x[j];
   weight[i] = x[0] * x[0] / s2;
+  if (vrow) {
+    const double inv = 1.0 / sqrt(s2);
+    for (int j = 0; j < nsteps; ++j) vrow[j] = j < n ? x[j] * inv : 0.0;
+  }
 }
 
 }  // namespace
@@ -138,8 +149,14 @@ size_t ritz_ws_bytes(long long nsteps) { return (size_t)6 * nsteps * nsteps * si
 
 int launch_ritz(const double* ab, const int* steps_done, int nsteps, double* theta, double* weight, void* ws,
                 void* stream) {
+  return launch_ritz_vectors(ab, steps_done, nsteps, theta, weight, ws, nullptr, stream);
+}
+
+int launch_ritz_vectors(const double* ab, const int* steps_done, int nsteps, double* theta, double* weight, void* ws,
+                        double* vecs, void* stream) {
   const int blocks = (nsteps + kRitzThreads - 1) / kRitzThreads;
-  ritz_kernel<<<blocks, kRitzThreads, 0, (cudaStream_t)stream>>>(ab, steps_done, nsteps, theta, weight, (double*)ws);
+  ritz_kernel<<<blocks, kRitzThreads, 0, (cudaStream_t)stream>>>(ab, steps_done, nsteps, theta, weight, (double*)ws,
+                                                                vecs);
   return (int)cudaGetLastError();
 }
 
