@@ -379,7 +379,8 @@ def run_secondary(args, dev, rank, world, peaks):
     from paper_1206_3518_gb300.pipeline import Forward
 
     out = {}
-    if world == 1 and not (args.no_screening and args.no_coupled and args.no_symmetry and args.no_tddft):
+    if world == 1 and not (args.no_screening and args.no_coupled and args.no_symmetry and args.no_tddft and
+                           args.no_states):
         spec, s = make_inputs(SECONDARY)
         plan = bse.Plan([spec])
         inf = plan.info(0)
@@ -400,6 +401,9 @@ def run_secondary(args, dev, rank, world, peaks):
             out["coupled"] = run_coupled(args, dev, spec, W, om, F, peaks)
         if not args.no_tddft:
             out["tddft"] = run_tddft(args, dev, spec, s, en, F, peaks)
+        if not args.no_states:
+            F.build(coef, en, W, spec.delta)
+            out["exciton_states"] = run_states(dev, spec, F, peaks)
         del F, coef, en, W, om
         torch.cuda.empty_cache()
     if not args.no_batch:
@@ -471,6 +475,41 @@ def run_tddft(args, dev, spec, s, en, F, peaks):
                               "work": "2 x 8 FP32 flops per complex MAC of nw ng0^2 dim"},
             "eps_m_static_rpa": float(er[i].real), "eps_m_static_alda": float(ea[i].real),
             "static_frequency_ha": float(s.omega[i])}
+
+
+def run_states(dev, spec, F, peaks):
+    """All eigenpairs of the workload's H (Eq. bse_eig) by the full-dimension Lanczos tridiagonalisation,
+    bisection, inverse iteration and back-transformation; CUDA-event time and the residual of the pairs."""
+    import numpy as np
+    import torch
+    from paper_1206_3518_gb300 import bse
+    plan = F.plan
+    dim = F.dim
+    n = dim
+    rng = np.random.default_rng(5)
+    x0 = torch.as_tensor(rng.standard_normal(dim) + 1j * rng.standard_normal(dim), device=dev)
+    theta = torch.empty(n, dtype=torch.float64, device=dev)
+    A = torch.empty(n, dim, dtype=torch.complex64, device=dev)
+    ab = torch.empty(2 * n, dtype=torch.float64, device=dev)
+    done = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(bse.bse_workspace_size(plan, 0, bse.BSE_WS_STATES, n) // 8 + 1, dtype=torch.complex64,
+                     device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    bse.bse_exciton_states(plan, 0, F.H, x0, n, theta, A, ab, done, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    bse.bse_status_read(plan)
+    ms = e0.elapsed_time(e1)
+    # residual |H A_l - theta_l A_l| / |H| on a sample of 64 states (row products on the device)
+    idx = torch.as_tensor(np.linspace(0, n - 1, 64).astype(np.int64), device=dev)
+    As = A[idx]
+    R = As @ F.H.transpose(0, 1) - theta[idx].to(torch.complex64)[:, None] * As
+    res = float(R.abs().max() / F.H.abs().max())
+    h_bytes = float(n) * 8.0 * dim * dim
+    return {"workload": f"{spec.name}, all {n} eigenpairs from a random start vector", "ms": ms,
+            "steps_done": int(done.item()), "residual_max_64_sampled": res,
+            "lanczos_h_stream_gbs_lower_bound": h_bytes / (ms / 1e3) / 1e9}
 
 
 def run_symmetry(plan, inf, W, dev):
@@ -1022,6 +1061,7 @@ def main():
     ap.add_argument("--no-coupled", action="store_true", help="skip the BSE with e-h / h-e coupling")
     ap.add_argument("--no-symmetry", action="store_true", help="skip the q-point symmetry measurement")
     ap.add_argument("--no-tddft", action="store_true", help="skip the TDDFT macroscopic dielectric function")
+    ap.add_argument("--no-states", action="store_true", help="skip the exciton-state eigensolver")
     ap.add_argument("--only", default="all", choices=["all", "pair", "spectrum", "contract"],
                     help="profiling aid: run one stage (pair: realspace + a q chunk of pair densities; "
                          "spectrum: Haydock on an H built once before the loop)")
