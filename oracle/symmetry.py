@@ -19,9 +19,21 @@ Readings:
 - The sphere of q maps onto the sphere of q_IBZ by G -> G' = s R^-1 (G + G0), s = +-1:
   q + G = s R (q_IBZ + G') keeps |q + G|.
 
+k-point symmetry of the e-h blocks.  When the states carry the point group (psi_{Tk}(r) = psi_k(T^-1 r),
+energies shared by the orbit of k) and W carries it too, Sec. III A's relation
+n_{nk,n'k+q}(G) = n_{nT^-1k,n'T^-1(k+q)}(T^-1(G0 + G)) makes the pair densities, and with them every
+kernel block, of the pair (k, k') equal to those of (Tk, Tk'): H_{Tk,Tk'} = H_{k,k'} block for block
+(same band indices; no phases for symmorphic operations).  ``reduce_blocks`` reads this as a reduction
+of the upper blocks: they are visited in row-major order (k ascending, then k' >= k); an unassigned
+block becomes a representative, then each operation in order maps it to (a, b) = (R k, R k') on the
+mesh and assigns the upper block (a, b) to it directly if a <= b, or (b, a) as its Hermitian mirror if
+a > b, when that block is still unassigned.  Time reversal is not used for the blocks.
+
 Pinned by tests/test_oracle_symmetry.py: group closure and metric, orbit sizes, invariance of the
 integer sphere keys under the map, bijective sphere permutations, and the Sec. III A relation for
-every operation of the group once W(q_IBZ) is made invariant under its little group.
+every operation of the group once W(q_IBZ) is made invariant under its little group; the block
+reduction covers every upper block once and, on a system whose states carry the group, the oracle's
+independent full Hamiltonian has every block equal to its representative (or its mirror).
 """
 from __future__ import annotations
 
@@ -113,3 +125,27 @@ def unfold_w(spec, W_ibz, ibz=None, qmap=None, ops=None):
         blk = W_ibz[qmap[iq][0]][np.ix_(perm, perm)]
         W[iq, :n, :n] = np.conj(blk) if qmap[iq][2] else blk
     return W
+
+
+def reduce_blocks(spec, ops=None):
+    """For every upper block (ik, ik2), ik <= ik2 in row-major order: (rep, mirrored) with rep the index of
+    its representative in the same order; returns (reps, table) with reps the representative indices."""
+    if ops is None:
+        ops = point_group(spec)
+    nk = np.asarray(spec.nk)
+    kr = geo.mesh_offsets(spec)
+    blocks = geo.upper_blocks(spec)
+    index = {b: i for i, b in enumerate(blocks)}
+    table = [None] * len(blocks)
+    reps = []
+    for i, (a0, b0) in enumerate(blocks):
+        if table[i] is not None:
+            continue
+        reps.append(i)
+        for R in ops:
+            a = geo.mesh_index(spec, np.mod(R @ kr[a0], nk))
+            b = geo.mesh_index(spec, np.mod(R @ kr[b0], nk))
+            j, mirrored = (index[(a, b)], 0) if a <= b else (index[(b, a)], 1)
+            if table[j] is None:
+                table[j] = (i, mirrored)
+    return reps, table

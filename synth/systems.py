@@ -52,6 +52,8 @@ class SystemSpec:
     dirac: bool = False       # slab: Dirac-like top valence / bottom conduction pair
     ev_range: tuple = (-6.0 * EV, 0.0)
     ec_range: tuple = (1.5 * EV, 10.0 * EV)
+    w_offdiag: float = 0.02   # scale of the random off-diagonal part of the model eps^-1
+    symmetric: bool = False   # states and energies carry the point group of the lattice (see below)
 
     @property
     def nb(self):
@@ -302,7 +304,7 @@ def _w_model(spec: SystemSpec, rng, kred, wdtype):
         if iq == 0:
             h[0, :] = 0.0
             h[:, 0] = 0.0
-        b = 0.02 * np.sqrt(np.outer(d, d)) * h / np.sqrt(ng)
+        b = spec.w_offdiag * np.sqrt(np.outer(d, d)) * h / np.sqrt(ng)
         if iq == iqb:
             g0p = (-iqv - iqb_v) // n
             pi_ = partner_index(iq, iqb, g0p)
@@ -362,12 +364,120 @@ def _v2d(spec, off, g, p2):
     return np.where(p2 > 0, v, 0.0)
 
 
+# --------------------------------------------------------------------------
+# symmetric systems: states and energies that carry the point group of the lattice
+# --------------------------------------------------------------------------
+
+def point_group(spec: SystemSpec) -> list:
+    """Integer 3x3 matrices R acting on reduced reciprocal coordinates (k -> R k) that keep the reciprocal
+    metric and map the k mesh onto itself, identity first, the others in ascending row-major order of
+    their entries (all entries in {-1, 0, 1})."""
+    bm = recip_lattice(spec)
+    M = bm @ bm.T
+    n = np.asarray(spec.nk)
+    ops = []
+    for code in range(3 ** 9):
+        c = code
+        e = np.zeros(9, dtype=np.int64)
+        for t in range(8, -1, -1):
+            e[t] = c % 3 - 1
+            c //= 3
+        R = e.reshape(3, 3)
+        if abs(round(np.linalg.det(R))) != 1:
+            continue
+        if np.abs(R.T @ M @ R - M).max() > 1e-9 * np.abs(M).max():
+            continue
+        if np.any((R * n[:, None]) % n[None, :] != 0):
+            continue
+        ops.append(R)
+    ident = np.eye(3, dtype=np.int64)
+    return [ident] + [R for R in ops if not np.array_equal(R, ident)]
+
+
+def _symmetric_states(spec: SystemSpec, rng, kred):
+    """Coefficients and energies with psi_{Rk}(r) = psi_k(R^-1 r) for every operation R of the point group
+    (no time reversal): c_{k'}(R G + G0) = c_k(G) where R k = k' + G0 on the mesh.  Random states are
+    drawn at the first k of each orbit (ascending index), projected onto the invariants of its little group
+    (the average over R with R k = k + G0 of c(R^-1 (G - G0))), orthonormalised (QR, diag(R) > 0: linear
+    combinations of invariant columns stay invariant) and copied to the other points of the orbit by the
+    first operation (in the order of point_group) that reaches them; energies are shared by the orbit."""
+    n = np.asarray(spec.nk, dtype=np.int64)
+    ops = point_group(spec)
+    inv = [np.rint(np.linalg.inv(R)).astype(np.int64) for R in ops]
+    nk = len(kred)
+
+    def lin(i):
+        return int((i[0] * n[1] + i[1]) * n[2] + i[2])
+
+    rep, opi = [-1] * nk, [-1] * nk
+    for ik in range(nk):
+        if rep[ik] >= 0:
+            continue
+        for io, R in enumerate(ops):
+            img = R @ kred[ik]
+            j = lin(np.mod(img, n))
+            if rep[j] < 0:
+                rep[j], opi[j] = ik, io
+    spheres = [sphere(spec, tuple(kred[ik])) for ik in range(nk)]
+
+    def index_of(g):
+        return {tuple(int(x) for x in v): t for t, v in enumerate(g)}
+
+    cols, energies = {}, np.zeros((nk, spec.nb))
+    for ik in range(nk):
+        if rep[ik] != ik:
+            continue
+        g, p2 = spheres[ik]
+        g = g.astype(np.int64)
+        pos = index_of(g)
+        z = (rng.standard_normal((len(g), spec.nb)) + 1j * rng.standard_normal((len(g), spec.nb))) / np.sqrt(2.0)
+        z *= np.exp(-p2 / 8.0)[:, None]
+        acc = np.zeros_like(z)
+        cnt = 0
+        for R, Ri in zip(ops, inv):
+            img = R @ kred[ik]
+            if np.any(np.mod(img, n) != kred[ik]):
+                continue
+            g0 = (img - kred[ik]) // n
+            src = [pos[tuple(int(x) for x in Ri @ (v - g0))] for v in g]
+            acc += z[src]
+            cnt += 1
+        z = acc / cnt
+        qm, rm = np.linalg.qr(z)
+        d = np.diag(rm)
+        qm = qm * (d / np.abs(d))[None, :]
+        cols[ik] = qm
+        energies[ik, : spec.nv] = np.sort(rng.uniform(spec.ev_range[0], spec.ev_range[1], spec.nv))
+        energies[ik, spec.nv:] = np.sort(rng.uniform(spec.ec_range[0], spec.ec_range[1], spec.nc))
+    gk, npw = [], []
+    coef = np.zeros((nk, spec.nb, max(len(sp[0]) for sp in spheres)), dtype=np.complex128)
+    for ik in range(nk):
+        r, R, Ri = rep[ik], ops[opi[ik]], inv[opi[ik]]
+        g = spheres[ik][0].astype(np.int64)
+        g0 = (R @ kred[r] - kred[ik]) // n
+        pos = index_of(spheres[r][0].astype(np.int64))
+        src = [pos[tuple(int(x) for x in Ri @ (v - g0))] for v in g]
+        coef[ik, :, : len(g)] = cols[r][src].T
+        energies[ik] = energies[r]
+        gk.append(spheres[ik][0])
+        npw.append(len(g))
+    return gk, np.array(npw, dtype=np.int64), coef, energies
+
+
 def generate(spec: SystemSpec, wdtype=np.complex128, with_w: bool = True) -> BulkSystem:
-    """Draw one system.  Order: coefficients (k ascending), energies (k ascending), W (q ascending)."""
+    """Draw one system.  Order: coefficients (k ascending), energies (k ascending), W (q ascending).
+    A symmetric spec draws its states on the first point of every orbit of the point group (see
+    _symmetric_states) and needs a model W without the random off-diagonal part (w_offdiag = 0), whose
+    entries depend only on |q + G| and |q + G'| and so carry the point group too."""
     rng = np.random.default_rng(spec.seed if not isinstance(spec.seed, tuple) else list(spec.seed))
     kred = kpoint_offsets(spec)
-    gk, npw, coef = _coefficients(spec, rng, kred)
-    energies = _energies(spec, rng, len(kred))
+    if spec.symmetric:
+        if spec.w_offdiag != 0.0 or spec.dirac:
+            raise ValueError("a symmetric system needs w_offdiag = 0 and no Dirac bands")
+        gk, npw, coef, energies = _symmetric_states(spec, rng, kred)
+    else:
+        gk, npw, coef = _coefficients(spec, rng, kred)
+        energies = _energies(spec, rng, len(kred))
     if spec.dirac:
         energies = _dirac_bands(spec, kred, energies)
     if with_w:

@@ -111,3 +111,68 @@ def test_unfolded_w_obeys_the_relation_for_every_operation(spec):
                 blk = W_ibz[ii][np.ix_(perm, perm)]
                 assert np.abs(W[iq, :n, :n] - (np.conj(blk) if tr else blk)).max() < 1e-12
         assert np.abs(W[iq, :n, :n] - W[iq, :n, :n].conj().T).max() < 1e-12
+
+
+def test_block_reduction_covers_every_upper_block_and_symmetric_h_repeats_it():
+    """k-point symmetry of the e-h blocks on a system whose states carry the point group (synthetic
+    symmetric states, diagonal model W): the oracle's full Hamiltonian, every block built independently,
+    has each upper block equal to its representative (mirrored blocks to its Hermitian conjugate)."""
+    from oracle import geometry as geo
+    from oracle import kernel as ok
+    from oracle import symmetry as sym
+    from synth import config_spec, generate
+    spec = config_spec("fcc_4x4x4_3v3c").replace(name="sym4", symmetric=True, w_offdiag=0.0, nsteps=20, nw=50)
+    s = generate(spec)
+    reps, table = sym.reduce_blocks(spec)
+    blocks = geo.upper_blocks(spec)
+    assert all(t is not None for t in table)
+    assert all(table[r] == (r, 0) for r in reps)
+    assert len(reps) < len(blocks) / 10                      # O_h: 2080 upper blocks reduce to a few dozen
+    H = ok.hamiltonian_full(spec, s.gk, s.coef, s.energies, s.W, spec.delta)
+    nvc = spec.nv * spec.nc
+    scale = np.abs(H).max()
+    worst = 0.0
+    for i, (a, b) in enumerate(blocks):
+        r, mir = table[i]
+        ra, rb = blocks[r]
+        ref = H[ra * nvc:(ra + 1) * nvc, rb * nvc:(rb + 1) * nvc]
+        if mir:
+            ref = ref.conj().T
+        worst = max(worst, np.abs(H[a * nvc:(a + 1) * nvc, b * nvc:(b + 1) * nvc] - ref).max())
+    assert worst < 1e-12 * scale
+    # a system without the symmetry does not repeat its blocks
+    s2 = generate(spec.replace(symmetric=False))
+    H2 = ok.hamiltonian_full(spec, s2.gk, s2.coef, s2.energies, s2.W, spec.delta)
+    i = next(j for j, t in enumerate(table) if t[0] != j)
+    r = table[i][0]
+    (a, b), (ra, rb) = blocks[i], blocks[r]
+    blk = H2[a * nvc:(a + 1) * nvc, b * nvc:(b + 1) * nvc]
+    ref = H2[ra * nvc:(ra + 1) * nvc, rb * nvc:(rb + 1) * nvc]
+    if table[i][1]:
+        ref = ref.conj().T
+    assert np.abs(blk - ref).max() > 0.1 * np.abs(ref).max()
+
+
+def test_symmetric_states_carry_the_group():
+    """c_{Rk}(R G + G0) = c_k(G) for every operation (R k = k' + G0 on the mesh) and shared energies."""
+    from oracle import geometry as geo
+    from oracle import symmetry as sym
+    from synth import config_spec, generate
+    spec = config_spec("fcc_4x4x4_3v3c").replace(name="sym4", symmetric=True, w_offdiag=0.0)
+    s = generate(spec)
+    ops = sym.point_group(spec)
+    nk = np.asarray(spec.nk)
+    kr = geo.mesh_offsets(spec)
+    worst = 0.0
+    for ik in (0, 1, 5, 21, 42):
+        pos = {tuple(int(x) for x in g): t for t, g in enumerate(s.gk[ik])}
+        for R in ops:
+            img = R @ kr[ik]
+            k2 = geo.mesh_index(spec, np.mod(img, nk))
+            g0 = (img - np.mod(img, nk)) // nk
+            pos2 = {tuple(int(x) for x in g): t for t, g in enumerate(s.gk[k2])}
+            for g, t in pos.items():
+                t2 = pos2[tuple(int(x) for x in R @ np.array(g) + g0)]
+                worst = max(worst, np.abs(s.coef[k2, :, t2] - s.coef[ik, :, t]).max())
+            assert np.array_equal(s.energies[k2], s.energies[ik])
+    assert worst < 1e-13
