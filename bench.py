@@ -406,9 +406,57 @@ def run_secondary(args, dev, rank, world, peaks):
             out["exciton_states"] = run_states(dev, spec, F, peaks)
         del F, coef, en, W, om
         torch.cuda.empty_cache()
+    if world == 1 and not args.no_symmetry:
+        out["kpoint_symmetry"] = run_kpoint_symmetry(dev)
     if not args.no_batch:
         out["batch"] = run_batch(args, dev, rank, world)
     return out
+
+
+def run_kpoint_symmetry(dev):
+    """k-point symmetry of the blocks (Sec. III A) on fcc 8x8x8 3v4c with states that carry the point group
+    and a diagonal model W: the build of every upper block against the build of the representatives plus
+    the fill stage, on the same inputs; CUDA-event times, H and eps_2 differences."""
+    import numpy as np
+    import torch
+    from paper_1206_3518_gb300 import bse
+    from paper_1206_3518_gb300.pipeline import Forward
+    from synth import config_spec, generate
+    spec = config_spec(SECONDARY).replace(name="fcc_8x8x8_3v4c_symmetric", symmetric=True, w_offdiag=0.0)
+    s = generate(spec, wdtype=np.complex64)
+    coef = torch.as_tensor(s.coef.astype(np.complex64), device=dev)
+    en = torch.as_tensor(s.energies, device=dev)
+    W = torch.as_tensor(s.W, device=dev)
+    om = torch.as_tensor(s.omega, device=dev)
+    res = {}
+    for label, sym_on in (("full", False), ("reduced", True)):
+        plan = bse.Plan([spec.replace(symmetric=sym_on)])
+        inf = plan.info(0)
+        F = Forward(plan, 0, nsteps=spec.nsteps, nw=spec.nw)
+        F.build(coef, en, W, spec.delta)
+        torch.cuda.synchronize()
+        bse.bse_status_read(plan)
+        times = []
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            F.build(coef, en, W, spec.delta)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        eps = F.spectrum(om, spec.eta).cpu().numpy().copy()
+        bse.bse_status_read(plan)
+        res[label] = {"build_ms": statistics.mean(times), "blocks_built": inf["nblocks"], "H": F.H.cpu().numpy(),
+                      "eps": eps}
+        del F, plan
+        torch.cuda.empty_cache()
+    dh = float(np.abs(res["reduced"]["H"] - res["full"]["H"]).max() / np.abs(res["full"]["H"]).max())
+    de = float(np.abs(res["reduced"]["eps"] - res["full"]["eps"]).max() / np.abs(res["full"]["eps"]).max())
+    return {"workload": f"{spec.name}: states carrying the 48 operations of the point group, diagonal model W",
+            "blocks_full": res["full"]["blocks_built"], "blocks_reduced": res["reduced"]["blocks_built"],
+            "build_ms_full": res["full"]["build_ms"], "build_ms_reduced": res["reduced"]["build_ms"],
+            "speedup": res["full"]["build_ms"] / res["reduced"]["build_ms"],
+            "H_rel_diff": dh, "eps2_rel_diff": de}
 
 
 def run_tddft(args, dev, spec, s, en, F, peaks):

@@ -89,6 +89,7 @@ typedef enum {
 #define BSE_BK_INIT      1u   /* A3 + A5 diagonal: H = diag + 2 K^x (upper)    */
 #define BSE_BK_DIRECT    2u   /* A4 + A5: H -= K^d for a q range, mirror       */
 #define BSE_BK_MIRROR    4u   /* A5 without A4: lower blocks and (B+B^H)/2      */
+#define BSE_BK_SYMFILL   8u   /* k-point symmetry: copy every other block from its representative */
 #define BSE_BC_INIT      1u   /* coupling: B = 2 Bx (upper block triangle)       */
 #define BSE_BC_DIRECT    2u   /* coupling: B -= Bd for a q range, mirror B^T     */
 #define BSE_BC_MIRROR    4u   /* coupling without Bd: lower blocks, (B+B^T)/2    */
@@ -113,6 +114,9 @@ typedef struct {
   int coulomb;          /* bse_coulomb: 3D 4pi/|G|^2 or slab-truncated 2D */
   double qhat[3];       /* optical-limit direction (Cartesian, normalised by the library) */
   double gap_floor;     /* Ha, floor of e_c - e_v in the dipole denominator */
+  int kpoint_symmetry;  /* 1: the states carry the lattice's point group (psi_{Rk}(r) = psi_k(R^-1 r),
+                           energies shared by each orbit) and W carries it too; the plan then keeps only
+                           the representative upper blocks (see BSE_BK_SYMFILL).  0: every upper block. */
 } bse_system;
 
 /* Sizes and strides of system s (filled by bse_plan_info). */
@@ -122,10 +126,12 @@ typedef struct {
   int ng_max;                 /* W row stride and pair-density vector stride */
   int ng0;                    /* size of the q = 0 sphere (exchange set) */
   int nq;                     /* = nkpt */
-  long long nblocks;          /* upper (k <= k') blocks */
+  long long nblocks;          /* upper (k <= k') blocks the plan builds (the representatives with k-point symmetry) */
   double omega_cell;          /* bohr^3 */
   double norm;                /* 1/(Omega Nk) */
   double prefactor;           /* C = 8 pi/(Omega Nk) */
+  int kpoint_symmetry;        /* the system's bse_system.kpoint_symmetry */
+  long long nfill;            /* upper blocks copied by BSE_BK_SYMFILL (0 without k-point symmetry) */
 } bse_info;
 
 typedef struct bse_plan bse_plan;
@@ -187,7 +193,8 @@ bse_status bse_rho_dir_count(const bse_plan* plan, int s, int q_begin, int q_end
  * P        complex128 [dim]: P_S = conj(qhat.sum_G conj(c_vk)(k+G)c_ck)/max(e_c-e_v, gap_floor).
  * rho_dir  complex64 [nvec][ng_max] for q in [q_begin, q_end): per q, first the
  *          nblk_q*nv*nv vectors rho~_vv'^{kk'} (block-major, then v, v'), then the
- *          nblk_q*nc*nc vectors rho~_cc'^{kk'}; entry p is taken at G = g_p(q) - G0,
+ *          nblk_q*nc*nc vectors rho~_cc'^{kk'} (nblk_q: the plan's blocks of q - with k-point
+ *          symmetry only the representatives); entry p is taken at G = g_p(q) - G0,
  *          g_p the p-th vector of the q sphere, so q_unf + G = q + g_p.
  * flags    BSE_PD_* stages; REALSPACE must run (once) before the others, with
  *          the same workspace.  Unused outputs may be NULL.  With BSE_PD_COUPLING (not with
@@ -212,6 +219,15 @@ bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags,
  * BSE_BK_MIRROR (not with DIRECT) completes an INIT-only build the same way: lower blocks
  * H_k'k = H_kk'^H, diagonal blocks (B + B^H)/2.  INIT | MIRROR is the Tamm-Dancoff form of the
  * random-phase response with local fields (exchange kernel only, no W).
+ * k-point symmetry (bse_system.kpoint_symmetry = 1; Sec. III A: the pair densities of (k, k') equal
+ * those of (Tk, Tk') on rotated G, so with symmetric states and W every block H_{Tk,Tk'} equals H_{k,k'}):
+ * the plan's blocks (bse_pair_blocks, bse_rho_dir_count, bse_plan_info nblocks) are only the
+ * representatives - the upper blocks in row-major order, each unassigned one a representative of
+ * the blocks (R k, R k') that the operations R (identity first, then ascending row-major entries)
+ * map it to, as the upper block itself when R k <= R k' and as its Hermitian mirror otherwise.
+ * DIRECT then builds only those; BSE_BK_SYMFILL (after every DIRECT chunk) copies each other upper
+ * block from its representative (or the representative's conjugate transpose) and writes its mirror.
+ * The coupling build and the adjoint need every block and return BSE_ERR_UNSUPPORTED for such plans.
  * W        complex64 [nq][ng_max][ng_max], W_q[p][p'] Hermitian, including 4 pi.
  * H        complex64 [dim][dim] row-major.
  * prec     BSE_PREC_FP32 (CUDA-core FP32) or BSE_PREC_BF16X3 (tcgen05 BF16

@@ -24,7 +24,7 @@ BSE_WS_PAIR, BSE_WS_KERNEL, BSE_WS_SPECTRUM, BSE_WS_BACKWARD, BSE_WS_SCREEN = 0,
 BSE_WS_COUPLING, BSE_WS_COUPLED, BSE_WS_RITZ = 5, 6, 7
 BSE_WS_CHI0, BSE_WS_ALDA, BSE_WS_EPSM, BSE_WS_STATES = 8, 9, 10, 11
 BSE_PD_REALSPACE, BSE_PD_EXCHANGE, BSE_PD_DIRECT, BSE_PD_CHI0, BSE_PD_COUPLING = 1, 2, 4, 8, 16
-BSE_BK_INIT, BSE_BK_DIRECT, BSE_BK_MIRROR = 1, 2, 4
+BSE_BK_INIT, BSE_BK_DIRECT, BSE_BK_MIRROR, BSE_BK_SYMFILL = 1, 2, 4, 8
 BSE_BC_INIT, BSE_BC_DIRECT, BSE_BC_MIRROR = 1, 2, 4
 
 EXPORTED = [
@@ -41,14 +41,15 @@ class BseSystem(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int), ("a", ctypes.c_double), ("c", ctypes.c_double),
                 ("nk", ctypes.c_int * 3), ("nv", ctypes.c_int), ("nc", ctypes.c_int),
                 ("ecut", ctypes.c_double), ("fft", ctypes.c_int * 3), ("coulomb", ctypes.c_int),
-                ("qhat", ctypes.c_double * 3), ("gap_floor", ctypes.c_double)]
+                ("qhat", ctypes.c_double * 3), ("gap_floor", ctypes.c_double), ("kpoint_symmetry", ctypes.c_int)]
 
 
 class BseInfo(ctypes.Structure):
     _fields_ = [("nkpt", ctypes.c_int), ("nb", ctypes.c_int), ("dim", ctypes.c_int),
                 ("npw_max", ctypes.c_int), ("ng_max", ctypes.c_int), ("ng0", ctypes.c_int),
                 ("nq", ctypes.c_int), ("nblocks", ctypes.c_longlong), ("omega_cell", ctypes.c_double),
-                ("norm", ctypes.c_double), ("prefactor", ctypes.c_double)]
+                ("norm", ctypes.c_double), ("prefactor", ctypes.c_double), ("kpoint_symmetry", ctypes.c_int),
+                ("nfill", ctypes.c_longlong)]
 
 
 class BsePairVariant(ctypes.Structure):
@@ -155,6 +156,7 @@ def system_struct(spec) -> BseSystem:
     s.coulomb = BSE_COULOMB_3D if spec.coulomb == "3d" else BSE_COULOMB_SLAB
     s.qhat[:] = list(getattr(spec, "qhat", (1.0, 0.0, 0.0)))
     s.gap_floor = float(getattr(spec, "gap_floor", 0.1 / 27.211386245988))
+    s.kpoint_symmetry = 1 if getattr(spec, "symmetric", False) else 0
     return s
 
 

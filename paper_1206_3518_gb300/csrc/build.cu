@@ -391,7 +391,36 @@ __global__ void cpl_mirror_kernel(DevSys d, float2* __restrict__ Bm) {
   }
 }
 
+// k-point symmetry: block (ik, ik2) = representative block (or its conjugate transpose), and the mirror
+// H_{ik2, ik} = H_{ik, ik2}^H; one CTA per listed block, one thread per element.
+__global__ void symfill_kernel(DevSys d, float2* __restrict__ H) {
+  const int4 f = d.fill[blockIdx.x];
+  const int nvc = d.nv * d.nc;
+  const bool mirrored = f.w < 0;
+  const int ra = f.z, rb = mirrored ? -f.w - 1 : f.w;
+  for (int t = threadIdx.x; t < nvc * nvc; t += blockDim.x) {
+    const int i = t / nvc, j = t - i * nvc;
+    float2 v;
+    if (mirrored) {
+      const float2 u = H[(size_t)(ra * nvc + j) * d.dim + rb * nvc + i];
+      v = make_float2(u.x, -u.y);
+    } else {
+      v = H[(size_t)(ra * nvc + i) * d.dim + rb * nvc + j];
+    }
+    H[(size_t)(f.x * nvc + i) * d.dim + f.y * nvc + j] = v;
+    if (f.x != f.y) H[(size_t)(f.y * nvc + j) * d.dim + f.x * nvc + i] = make_float2(v.x, -v.y);
+  }
+}
 }  // namespace
+
+int launch_symfill(const DevSys& d, void* H, void* stream) {
+  if (d.nfill <= 0) return 0;
+  if (d.nfill >= (1LL << 31)) return (int)cudaErrorInvalidValue;
+  const int nvc = d.nv * d.nc;
+  symfill_kernel<<<(unsigned)d.nfill, nvc * nvc < 256 ? (nvc * nvc + 31) / 32 * 32 : 256, 0, (cudaStream_t)stream>>>(
+      d, (float2*)H);
+  return (int)cudaGetLastError();
+}
 
 int launch_mirror(const DevSys& d, void* H, void* stream) {
   mirror_kernel<<<1216, 256, 0, (cudaStream_t)stream>>>(d, (float2*)H);
@@ -443,6 +472,8 @@ int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin
   const int side_c = (d.nc * d.nc < d.nv * d.nv) ? 1 : 0;
   cudaStream_t st = (cudaStream_t)stream;
   int e;
+  if (prec != BSE_PREC_BF16X3 && prec != BSE_PREC_FP32) return -1;
+  if (b_count <= 0 || max_rows <= 0) return 0;     // no block in the range (k-point symmetry can leave q empty)
   if (prec == BSE_PREC_BF16X3) {
     void* split_ws = (char*)ws + x_bytes(d, q_end - q_begin, direct_width(d));
     e = launch_gemm_wr_tc(d, rho_dir, q_begin, q_end, vbase, max_rows, W, ws, split_ws, side_c, status, stream);

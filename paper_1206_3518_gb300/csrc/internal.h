@@ -37,10 +37,15 @@ struct DevSys {
   const int* qperm;               // [nq][ng_max] sphere map of q onto its irreducible point (-1 padded)
   const int2* qsym;               // [nq] (irreducible index, time reversal)
   int nibz;
+  // k-point symmetry: the upper blocks that are not representatives, (ik, ik2, rep ik, rep ik2), the last
+  // stored as -(rep ik2 + 1) when the block is the representative's Hermitian mirror
+  const int4* fill;
+  long long nfill;
 };
 
 struct SysPlan {
   bse_system sys;
+  std::vector<int4> fill;                      // host copy of DevSys::fill
   DevSys d;                       // device view (pointers valid on the plan's device)
   std::vector<std::vector<int32_t>> gk, gq;   // host spheres, flattened (g1,g2,g3)*
   std::vector<int32_t> blocks;                 // host (ik, ik2, iq, g0x, g0y, g0z) per block
@@ -88,6 +93,7 @@ int pair_variant_current(const DevSys& d);
 
 int launch_kernel_init(const DevSys& d, const void* rho_x, const double* energies, double delta, void* H, void* stream);
 int launch_mirror(const DevSys& d, void* H, void* stream);
+int launch_symfill(const DevSys& d, void* H, void* stream);
 int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long b_begin,
                                long long b_count, long long vbase, long long max_rows, const void* W, int prec,
                                void* H, void* ws, int* status, void* stream);

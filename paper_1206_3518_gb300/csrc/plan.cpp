@@ -236,17 +236,6 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
       if (kn > 0.0 && t < ng_max) h_vsq[(size_t)ik * ng_max + t] = (float)(std::sqrt(4.0 * kPi) / kn);
     }
   }
-  std::vector<int4> h_blocks(d.nblocks);
-  for (long long i = 0; i < d.nblocks; ++i) {
-    const int32_t* r = &sp.blocks[6 * i];
-    const int packed = (r[3] + 1) | ((r[4] + 1) << 2) | ((r[5] + 1) << 4);
-    h_blocks[i] = make_int4(r[0], r[1], r[2], packed);
-  }
-  std::vector<int> h_blkidx((size_t)nkpt * nkpt, -1);
-  for (long long i = 0; i < d.nblocks; ++i) {
-    const int32_t* r = &sp.blocks[6 * i];
-    h_blkidx[(size_t)r[2] * nkpt + r[0]] = (int)i;
-  }
   std::vector<float> h_xs(ng_max, 0.0f);
   for (int t = 1; t < d.ng0; ++t) {
     const int* g = &sp.gq[0][3 * t];
@@ -363,6 +352,84 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
     d.nibz = (int)sp.ibz.size();
   }
 
+  // ---- k-point symmetry of the blocks (Sec. III A) ----
+  // With states that carry the point group, H_{Rk,Rk'} = H_{k,k'}: upper blocks visited in row-major
+  // order, an unassigned block becomes a representative, and each operation in order assigns the
+  // upper block of (R k, R k') to it (directly if R k <= R k', as the Hermitian mirror otherwise).
+  // The plan keeps only the representatives; the others are listed for the fill stage.
+  d.nfill = 0;
+  sp.fill.clear();
+  if (s.kpoint_symmetry) {
+    const int nops = (int)sp.ops.size();
+    std::vector<int> img((size_t)nops * nkpt);
+    for (int io = 0; io < nops; ++io) {
+      const auto& r = sp.ops[io];
+      for (int ik = 0; ik < nkpt; ++ik) {
+        int o[3], f[3];
+        offs(ik, o);
+        for (int i = 0; i < 3; ++i) {
+          const int v = r[3 * i] * o[0] + r[3 * i + 1] * o[1] + r[3 * i + 2] * o[2];
+          f[i] = ((v % s.nk[i]) + s.nk[i]) % s.nk[i];
+        }
+        img[(size_t)io * nkpt + ik] = (f[0] * nk2 + f[1]) * nk3 + f[2];
+      }
+    }
+    auto up_index = [&](long long a, long long b2) { return a * nkpt - a * (a - 1) / 2 + (b2 - a); };
+    const long long nup = (long long)nkpt * (nkpt + 1) / 2;
+    std::vector<long long> rep(nup, -1);
+    std::vector<char> mir(nup, 0);
+    std::vector<int2> pair_of(nup);
+    long long idx = 0;
+    for (int a0 = 0; a0 < nkpt; ++a0)
+      for (int b0 = a0; b0 < nkpt; ++b0, ++idx) {
+        pair_of[idx] = make_int2(a0, b0);
+        if (rep[idx] >= 0) continue;
+        for (int io = 0; io < nops; ++io) {
+          const int a = img[(size_t)io * nkpt + a0], b2 = img[(size_t)io * nkpt + b0];
+          const long long j = a <= b2 ? up_index(a, b2) : up_index(b2, a);
+          if (rep[j] < 0) {
+            rep[j] = idx;
+            mir[j] = a <= b2 ? 0 : 1;
+          }
+        }
+      }
+    for (long long j = 0; j < nup; ++j) {
+      if (rep[j] == j) continue;
+      const int2 p = pair_of[j], r = pair_of[rep[j]];
+      sp.fill.push_back(make_int4(p.x, p.y, r.x, mir[j] ? -(r.y + 1) : r.y));
+    }
+    d.nfill = (long long)sp.fill.size();
+    std::vector<int32_t> kept;
+    std::vector<long long> qb(nkpt + 1, 0), qv(nkpt + 1, 0);
+    const long long per_blk = (long long)s.nv * s.nv + (long long)s.nc * s.nc;
+    for (int iq = 0; iq < nkpt; ++iq) {
+      long long nb = 0;
+      for (long long i = sp.qblk_off[iq]; i < sp.qblk_off[iq + 1]; ++i) {
+        const int32_t* r = &sp.blocks[6 * i];
+        if (rep[up_index(r[0], r[1])] != up_index(r[0], r[1])) continue;
+        kept.insert(kept.end(), r, r + 6);
+        ++nb;
+      }
+      qb[iq + 1] = qb[iq] + nb;
+      qv[iq + 1] = qv[iq] + nb * per_blk;
+    }
+    sp.blocks = kept;
+    sp.qblk_off = qb;
+    sp.qvec_off = qv;
+    d.nblocks = qb[nkpt];
+  }
+  std::vector<int4> h_blocks(d.nblocks > 0 ? d.nblocks : 1);
+  for (long long i = 0; i < d.nblocks; ++i) {
+    const int32_t* r = &sp.blocks[6 * i];
+    const int packed = (r[3] + 1) | ((r[4] + 1) << 2) | ((r[5] + 1) << 4);
+    h_blocks[i] = make_int4(r[0], r[1], r[2], packed);
+  }
+  std::vector<int> h_blkidx((size_t)nkpt * nkpt, -1);
+  for (long long i = 0; i < d.nblocks; ++i) {
+    const int32_t* r = &sp.blocks[6 * i];
+    h_blkidx[(size_t)r[2] * nkpt + r[0]] = (int)i;
+  }
+
   // -G on the q = 0 sphere (coupling exchange, Bx)
   std::vector<int> h_gm0(d.ng0 > 0 ? d.ng0 : 1, -1);
   {
@@ -394,6 +461,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   for (int iq = 0; iq < nkpt; ++iq) h_qsym[iq] = make_int2(sp.qmap[6 * iq], sp.qmap[6 * iq + 2]);
   const size_t o_qp = off; off = align256(off + sp.qperm.size() * sizeof(int));
   const size_t o_qs = off; off = align256(off + h_qsym.size() * sizeof(int2));
+  const size_t o_fill = off; off = align256(off + (sp.fill.empty() ? 1 : sp.fill.size()) * sizeof(int4));
   char* base = nullptr;
   bse_status st = cuda_check(cudaMalloc((void**)&base, off), "cudaMalloc(plan tables)");
   if (st != BSE_OK) return st;
@@ -414,6 +482,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   if (!err) err = up(o_gm0, h_gm0.data(), h_gm0.size() * sizeof(int));
   if (!err) err = up(o_qp, sp.qperm.data(), sp.qperm.size() * sizeof(int));
   if (!err) err = up(o_qs, h_qsym.data(), h_qsym.size() * sizeof(int2));
+  if (!err) err = up(o_fill, sp.fill.data(), sp.fill.size() * sizeof(int4));
   if ((st = cuda_check(err, "cudaMemcpy(plan tables)")) != BSE_OK) return st;
   d.gk = (const char4*)(base + o_gk);
   d.npw = (const int*)(base + o_npw);
@@ -429,6 +498,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   d.gminus0 = (const int*)(base + o_gm0);
   d.qperm = (const int*)(base + o_qp);
   d.qsym = (const int2*)(base + o_qs);
+  d.fill = (const int4*)(base + o_fill);
   return BSE_OK;
 }
 
@@ -512,6 +582,8 @@ bse_status bse_plan_info(const bse_plan* plan, int s, bse_info* info) {
   info->omega_cell = d.omega_cell;
   info->norm = d.norm;
   info->prefactor = d.prefactor;
+  info->kpoint_symmetry = plan->sys[s].sys.kpoint_symmetry ? 1 : 0;
+  info->nfill = d.nfill;
   return BSE_OK;
 }
 
@@ -639,6 +711,8 @@ bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags, const void*
     return set_error(BSE_ERR_ARG, "BSE_PD_DIRECT, BSE_PD_CHI0 and BSE_PD_COUPLING all write rho_dir");
   if (flags & BSE_PD_COUPLING) {
     if (!rho_dir || q_begin < 0 || q_end > d.nq || q_begin >= q_end) return set_error(BSE_ERR_ARG, "bad coupling range");
+    if (sp.sys.kpoint_symmetry)
+      return set_error(BSE_ERR_UNSUPPORTED, "the coupling densities are built without k-point symmetry");
     const long long vb = 2LL * d.nv * d.nc * sp.qblk_off[q_begin];
     if ((st = cuda_check(launch_pair_coupling(d, ws, rho_dir, q_begin, q_end, vb, plan->d_status, stream),
                          "pair coupling")) != BSE_OK)
@@ -778,6 +852,10 @@ bse_status bse_build_kernel(bse_plan* plan, int s, unsigned flags, const void* r
     if (flags & BSE_BK_DIRECT) return set_error(BSE_ERR_ARG, "the direct stage already mirrors its blocks");
     if ((st = cuda_check(launch_mirror(d, H, stream), "kernel mirror")) != BSE_OK) return st;
   }
+  if (flags & BSE_BK_SYMFILL) {
+    if (!plan->sys[s].sys.kpoint_symmetry) return set_error(BSE_ERR_ARG, "BSE_BK_SYMFILL needs a plan with k-point symmetry");
+    if ((st = cuda_check(launch_symfill(d, H, stream), "symmetry fill")) != BSE_OK) return st;
+  }
   return BSE_OK;
 }
 
@@ -879,6 +957,8 @@ bse_status bse_spectrum_backward(bse_plan* plan, int s, const void* H, const voi
   if (nsteps > d.dim) return set_error(BSE_ERR_ARG, "nsteps > dim");
   if ((dL_drho_x && !rho_x) || ((dL_drho_dir || dL_dW) && (!rho_dir || !W)))
     return set_error(BSE_ERR_ARG, "chained gradients need their forward inputs");
+  if (plan->sys[s].sys.kpoint_symmetry && (dL_drho_dir || dL_dW))
+    return set_error(BSE_ERR_UNSUPPORTED, "the adjoint chain through the direct term needs every block (k-point symmetry plan)");
   if (!ws || ws_bytes < backward_ws_bytes(d, nsteps)) return set_error(BSE_ERR_WORKSPACE, "backward workspace too small");
   if ((st = scan_input(plan, H, 2LL * d.dim * d.dim, 4, stream)) != BSE_OK) return st;
   if ((st = scan_input(plan, P, 2LL * d.dim, 8, stream)) != BSE_OK) return st;
@@ -932,6 +1012,8 @@ bse_status bse_build_coupling(bse_plan* plan, int s, unsigned flags, const void*
   if (!Bm) return set_error(BSE_ERR_ARG, "Bm is NULL");
   if (prec != BSE_PREC_FP32 && prec != BSE_PREC_BF16X3) return set_error(BSE_ERR_ARG, "unknown precision");
   if (d.nv * d.nc > 16) return set_error(BSE_ERR_UNSUPPORTED, "coupling blocks are built for Nv Nc <= 16");
+  if (sp.sys.kpoint_symmetry && (flags & BSE_BC_DIRECT))
+    return set_error(BSE_ERR_UNSUPPORTED, "the coupling block is built without k-point symmetry");
   if ((flags & BSE_BC_DIRECT) && (flags & BSE_BC_MIRROR))
     return set_error(BSE_ERR_ARG, "the direct stage already mirrors its blocks");
   if (flags & BSE_BC_INIT) {

@@ -56,6 +56,8 @@ class Forward:
             bse.bse_pair_densities(p, s, bse.BSE_PD_DIRECT, None, None, None, None, self.rho_dir, q0, q1, self.ws_pair)
             bse.bse_build_kernel(p, s, bse.BSE_BK_DIRECT, None, self.rho_dir, q0, q1, W, None, delta, prec, self.H,
                                  self.ws_kernel)
+        if self.info["kpoint_symmetry"]:
+            bse.bse_build_kernel(p, s, bse.BSE_BK_SYMFILL, None, None, 0, 0, None, None, delta, prec, self.H, None)
         return self.H
 
     def spectrum(self, omega, eta, nsteps=None):

@@ -77,3 +77,51 @@ def test_unfold_bit_exact_and_hamiltonian_from_irreducible_w(bse, cfg1):
     Href = ok.hamiltonian_from_factors(spec, cfg1.energies, spec.delta, rx, ok.direct_factors(spec, cfg1.gk, cfg1.coef),
                                        W_ref.astype(np.complex128))
     assert np.abs(H - Href).max() / np.abs(Href).max() < 1e-5
+
+
+def test_kpoint_symmetry_reduced_build_matches_oracle(bse):
+    """States that carry the point group (fcc 4x4x4 3v3c, diagonal model W): the plan builds only the 92
+    representative blocks of 2080 and copies the rest (BSE_BK_SYMFILL); H against the oracle's
+    independent full build (1e-5), and H and eps_2 against the GPU's own full build of the same system."""
+    from oracle import kernel as ok
+    from oracle import pair as op
+    from oracle import spectrum as osp
+    from paper_1206_3518_gb300.pipeline import Forward
+    from synth import config_spec
+    spec = config_spec("fcc_4x4x4_3v3c").replace(name="sym4", symmetric=True, w_offdiag=0.0)
+    s = generate(spec)
+    dev = lambda x, t: torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=t)  # noqa: E731
+    coef, en, W = dev(s.coef, torch.complex64), dev(s.energies, torch.float64), dev(s.W, torch.complex64)
+    om = dev(s.omega, torch.float64)
+    out = {}
+    for sym_on in (True, False):
+        plan = bse.Plan([spec.replace(symmetric=sym_on)])
+        inf = plan.info(0)
+        F = Forward(plan, 0, nsteps=spec.nsteps, nw=spec.nw, qchunk=16)
+        F.build(coef, en, W, spec.delta)
+        eps = F.spectrum(om, spec.eta).cpu().numpy().copy()
+        bse.bse_status_read(plan)
+        out[sym_on] = (F.H.cpu().numpy(), eps, inf["nblocks"])
+    Href = ok.hamiltonian_full(spec, s.gk, s.coef, s.energies, s.W, spec.delta)
+    Hs, es, nrep = out[True]
+    Hf, ef, nall = out[False]
+    assert nrep == 92 and nall == 2080
+    assert np.array_equal(Hs, Hs.conj().T)
+    err_ref = np.abs(Hs - Href).max() / np.abs(Href).max()
+    err_full = np.abs(Hs - Hf).max() / np.abs(Hf).max()
+    P = op.dipole(spec, s.gk, s.coef, s.energies)
+    # the spectrum of the reduced build against the oracle's FP64 recursion on the same H; the symmetric H is
+    # highly degenerate (270 distinct eigenvalues of 576), which makes the 100-step truncated recursion
+    # sensitive to the FP32 rounding of H: the bound is 10x the change that storing the oracle's own H in
+    # FP32 makes (computed from the oracle alone)
+    eref = osp.eps2_haydock(spec, Hs.astype(np.complex128), P, s.omega, spec.eta, spec.nsteps)[0]
+    e64 = osp.eps2_haydock(spec, Href, P, s.omega, spec.eta, spec.nsteps)[0]
+    e32 = osp.eps2_haydock(spec, Href.astype(np.complex64).astype(np.complex128), P, s.omega, spec.eta,
+                           spec.nsteps)[0]
+    floor = np.abs(e32 - e64).max() / e64.max()
+    err_e = np.abs(es - eref).max() / eref.max()
+    print(f"k-point symmetry: {nrep} of {nall} blocks built; H vs oracle {err_ref:.2e}, vs the full GPU build "
+          f"{err_full:.2e}; eps_2 vs the oracle's recursion on the same H {err_e:.2e} (FP32-storage floor "
+          f"{floor:.2e}); vs the full build's eps_2 {np.abs(es - ef).max() / ef.max():.2e}")
+    assert err_ref < 1e-5 and err_full < 1e-5
+    assert err_e < max(1e-5, 10.0 * floor)

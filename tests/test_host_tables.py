@@ -161,3 +161,21 @@ def test_bench_pair_work_counts_the_correlation_loop(bse, cfg1):
         iq, iqv, _ = geo.fold(spec, kr[ik], kr[ik2])
         cmac += len(geo.sphere(spec, tuple(iqv))) * npw[ik2]
     assert pw["cmac"] == cmac * (spec.nv ** 2 + spec.nc ** 2)
+
+
+def test_kpoint_symmetry_representatives_match_oracle(bse):
+    """With k-point symmetry the plan keeps exactly the oracle's representative upper blocks."""
+    from oracle import symmetry as sym
+    for name in ("fcc_4x4x4_3v3c", "fcc_8x8x8_3v4c"):
+        spec = config_spec(name).replace(symmetric=True, w_offdiag=0.0)
+        plan = bse.Plan([spec], host_only=True)
+        inf = plan.info(0)
+        reps, _ = sym.reduce_blocks(spec)
+        blocks = geo.upper_blocks(spec)
+        got = set()
+        for q in range(spec.nkpt):
+            b, _ = bse.bse_pair_blocks(plan, 0, q)
+            got |= {(int(x), int(y)) for x, y in b}
+        assert got == {blocks[r] for r in reps}
+        assert inf["kpoint_symmetry"] == 1 and inf["nblocks"] == len(reps)
+        assert inf["nblocks"] + inf["nfill"] == len(blocks)
