@@ -376,9 +376,10 @@ bse_status bse_spectrum_backward(bse_plan* plan, int s, const void* H, const voi
 /*
  * Tile-shape variants of the pair-density kernel (step A2) and their autotuner.
  *
- * Two routes compute the pair densities.  The plane-wave correlation kernel (variant indices 64
- * and 65, listed first with rows = 0; 65 issues the gather of the next G2 row one iteration ahead,
- * 64 does not, and both give bit-identical results) sums conj(c_nk(G2 - G)) c_mk'(G2) over the
+ * Two routes compute the pair densities.  The plane-wave correlation kernel (variant indices 64,
+ * 65 and 66, listed first with rows = 0; 65 issues the gather of the next G2 row one iteration ahead,
+ * 64 does not; 66 computes the vv' and cc' products of a direct-set block in two CTAs, two per SM,
+ * and is listed where that fits shared memory; all three give bit-identical results) sums conj(c_nk(G2 - G)) c_mk'(G2) over the
  * sphere of k' with a shared-memory index box of the sphere of k; it is compiled for Nv, Nc in
  * {1..3} x {1..3}, (3, 4), (4, 4) and is the default where valid.  The pruned-FFT kernels (the paper's route) are
  * compiled per real-space grid (threads per CTA, z-lines per chunk, maximum band products and

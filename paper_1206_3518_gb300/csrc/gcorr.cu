@@ -56,13 +56,28 @@ struct Shape {
   }
 };
 
+// Direct set split over two CTAs per block (vv' or cc'): NBG bands at k and at k', all NBG^2 products to
+// the output of group GROUP (0: out_v, 1: out_c).  Half the accumulators of the merged shape, so two
+// CTAs share an SM.
+template <int NBG, int GROUP>
+struct SplitShape {
+  static constexpr int NA = NBG;
+  static constexpr int NK = NBG;
+  static constexpr int NKP = (NK + 1) & ~1;
+  static constexpr int RS = (((NA + 1) & ~1) / 2) % 2 == 1 ? ((NA + 1) & ~1) : ((NA + 1) & ~1) + 2;
+  static constexpr int P = NBG * NBG;
+  static constexpr int a(int p) { return p / NBG; }
+  static constexpr int b(int p) { return p % NBG; }
+  static constexpr int o(int) { return GROUP; }
+  static constexpr int t(int p) { return p; }
+};
+
 struct Box {
   int rx, ry, rz, dy, dz, n;   // key (g1, g2, g3) -> ((g1 + rx) dy + g2 + ry) dz + g3 + rz
 };
 
-template <int NV, int NC, int KIND>
-size_t smem_bytes(const DevSys& d, const Box& bx) {
-  using S = Shape<NV, NC, KIND>;
+template <class S>
+size_t shape_smem_bytes(const DevSys& d, const Box& bx) {
   const size_t ca = (size_t)S::RS * (d.npw_max + 1) * sizeof(float2);
   const size_t cb = (size_t)d.npw_max * S::NKP * sizeof(float2);
   const size_t lin = (size_t)d.npw_max * sizeof(int);
@@ -70,12 +85,21 @@ size_t smem_bytes(const DevSys& d, const Box& bx) {
   return ((ca + 15) & ~(size_t)15) + cb + lin + box;
 }
 
+template <int NV, int NC, int KIND>
+size_t smem_bytes(const DevSys& d, const Box& bx) {
+  return shape_smem_bytes<Shape<NV, NC, KIND>>(d, bx);
+}
+
+template <int NV, int NC>
+size_t split_smem_bytes(const DevSys& d, const Box& bx) {
+  return NV >= NC ? shape_smem_bytes<SplitShape<NV, 0>>(d, bx) : shape_smem_bytes<SplitShape<NC, 1>>(d, bx);
+}
+
 // Diagonal blocks (k = k', q = 0, G0 = 0): the first sphere point is G = 0, where the overlaps
 // rho_nm^{kk}(0) are delta_nm (0 for the coupling set) up to rounding and meet the q = 0 head of W
 // (~1e4 Ha bohr^3 for the slab workloads).  One warp sums them again with FP64 accumulation.
-template <int NV, int NC, int KIND>
+template <class S>
 __device__ __noinline__ void g0_overlaps(const float2* ca, const float2* cb2, int n2, const Job& jb, int ng_max) {
-  using S = Shape<NV, NC, KIND>;
   const int lane = threadIdx.x & 31;
   for (int q = 0; q < S::P; ++q) {
     double sr = 0.0, si = 0.0;
@@ -96,14 +120,11 @@ __device__ __noinline__ void g0_overlaps(const float2* ca, const float2* cb2, in
   }
 }
 
-template <int NV, int NC, int KIND, int PF>
-__global__ __launch_bounds__(kGcMaxThreads) void gcorr_kernel(DevSys d, const float2* __restrict__ coef,
-                                                              float2* __restrict__ out, int mode, int q0, int nqc,
-                                                              long long vbase, Box bx) {
-  using S = Shape<NV, NC, KIND>;
+// One job: shared-memory setup, then every sphere point of q over the sphere of k' (see top of file).
+template <class S, int PF, bool OVERLAPS>
+__device__ __forceinline__ void corr_body(const DevSys& d, const float2* __restrict__ coef, const Job& jb,
+                                          const Box& bx) {
   constexpr int NA = S::NA, NK = S::NK, NKP = S::NKP, P = S::P;
-  Job jb;
-  if (!decode_job(d, mode, true, q0, nqc, vbase, out, jb)) return;
   extern __shared__ __align__(16) float4 smv[];
   constexpr int RS = S::RS;
   float2* ca = reinterpret_cast<float2*>(smv);         // [npw_max + 1][RS]: k bands per G1; row npw_max is zero
@@ -220,23 +241,47 @@ __global__ __launch_bounds__(kGcMaxThreads) void gcorr_kernel(DevSys d, const fl
         dst[p] = make_float2(acc[2 * q], acc[2 * q + 1]);
       }
     }
-    if (KIND != 0 && p0 == 0 && tid < 32 && jb.k == jb.k2) {
+    if (OVERLAPS && p0 == 0 && tid < 32 && jb.k == jb.k2) {
       const char4 g = d.gq[(size_t)jb.q * d.ng_max];
       if (g.x == 0 && g.y == 0 && g.z == 0 && jb.g0x == 0 && jb.g0y == 0 && jb.g0z == 0) {
         __syncwarp();
-        g0_overlaps<NV, NC, KIND>(ca, cb2, n2, jb, d.ng_max);
+        g0_overlaps<S>(ca, cb2, n2, jb, d.ng_max);
       }
     }
   }
 }
 
+template <int NV, int NC, int KIND, int PF>
+__global__ __launch_bounds__(kGcMaxThreads) void gcorr_kernel(DevSys d, const float2* __restrict__ coef,
+                                                              float2* __restrict__ out, int mode, int q0, int nqc,
+                                                              long long vbase, Box bx) {
+  Job jb;
+  if (!decode_job(d, mode, true, q0, nqc, vbase, out, jb)) return;
+  corr_body<Shape<NV, NC, KIND>, PF, KIND != 0>(d, coef, jb, bx);
+}
+
+// Direct set with the vv' and cc' products of a block in separate CTAs (two CTAs per SM).
+template <int NV, int NC>
+__global__ __launch_bounds__(kGcMaxThreads, 2) void gcorr_split_kernel(DevSys d, const float2* __restrict__ coef,
+                                                                      float2* __restrict__ out, int mode, int q0,
+                                                                      int nqc, long long vbase, Box bx) {
+  Job jb;
+  if (!decode_job(d, mode, false, q0, nqc, vbase, out, jb)) return;
+  if (jb.mode == 1)
+    corr_body<SplitShape<NV, 0>, 0, true>(d, coef, jb, bx);
+  else
+    corr_body<SplitShape<NC, 1>, 0, true>(d, coef, jb, bx);
+}
+
 typedef void (*GcFn)(DevSys, const float2*, float2*, int, int, int, long long, Box);
 
-// fn[kind][pf]: pf = 1 is the software-pipelined gather
+// fn[kind][pf]: pf = 1 is the software-pipelined gather; split: the direct set in two CTAs per block
 struct GcEntry {
   int nv, nc;
   GcFn fn[3][2];
   size_t (*smem[3])(const DevSys&, const Box&);
+  GcFn split;
+  size_t (*split_smem)(const DevSys&, const Box&);
 };
 
 #define BSE_GC(NV, NC)                                                                                   \
@@ -245,7 +290,8 @@ struct GcEntry {
         {{gcorr_kernel<NV, NC, 0, 0>, gcorr_kernel<NV, NC, 0, 1>},                                       \
          {gcorr_kernel<NV, NC, 1, 0>, gcorr_kernel<NV, NC, 1, 1>},                                       \
          {gcorr_kernel<NV, NC, 2, 0>, gcorr_kernel<NV, NC, 2, 1>}},                                      \
-        {smem_bytes<NV, NC, 0>, smem_bytes<NV, NC, 1>, smem_bytes<NV, NC, 2>}                            \
+        {smem_bytes<NV, NC, 0>, smem_bytes<NV, NC, 1>, smem_bytes<NV, NC, 2>}, gcorr_split_kernel<NV, NC>,  \
+        split_smem_bytes<NV, NC>                                                                         \
   }
 
 // band counts compiled: the fcc workloads (3v3c, 3v4c, 4v4c, the 2v2c test cell) and every
@@ -289,19 +335,26 @@ int gcorr_valid(const DevSys& d) {
   return 1;
 }
 
+// The split direct-set kernel fits two CTAs per SM when its shared memory does.
+int gcorr_split_valid(const DevSys& d) {
+  const GcEntry* e = find(d);
+  if (!e || !gcorr_valid(d)) return 0;
+  return e->split_smem(d, box_of(d)) <= 113 * 1024 ? 1 : 0;
+}
+
 int gcorr_threads(const DevSys& d) { return threads_of(d); }
 
-// kind 0: exchange / screening sets, 1: direct set, 2: coupling set; cells = CTAs of the launch;
-// pf = 1: the software-pipelined gather.
+// kind 0: exchange / screening sets, 1: direct set, 2: coupling set, 3: direct set split over two CTAs per
+// block (cells must count both); cells = CTAs of the launch; pf = 1: the software-pipelined gather.
 int launch_gcorr(const DevSys& d, const void* coef, void* out, int kind, int mode, int q0, int nqc, long long vbase,
                  long long cells, int pf, void* stream) {
   const GcEntry* e = find(d);
-  if (!e || kind < 0 || kind > 2) return (int)cudaErrorInvalidValue;
+  if (!e || kind < 0 || kind > 3) return (int)cudaErrorInvalidValue;
   if (cells <= 0) return 0;
   if (cells >= (1LL << 31)) return (int)cudaErrorInvalidValue;
   const Box bx = box_of(d);
-  const size_t sm = e->smem[kind](d, bx);
-  const GcFn fn = e->fn[kind][pf ? 1 : 0];
+  const size_t sm = kind == 3 ? e->split_smem(d, bx) : e->smem[kind](d, bx);
+  const GcFn fn = kind == 3 ? e->split : e->fn[kind][pf ? 1 : 0];
   int err = (int)cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (err) return err;
   fn<<<(unsigned)cells, threads_of(d), sm, (cudaStream_t)stream>>>(d, (const float2*)coef, (float2*)out,

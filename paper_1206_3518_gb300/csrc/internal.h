@@ -83,6 +83,7 @@ int launch_screening(const DevSys& d, void* rho_chi, const double* energies, con
 int pair_supported(const DevSys& d);
 size_t pair_ws_bytes(const DevSys& d);
 int gcorr_valid(const DevSys& d);
+int gcorr_split_valid(const DevSys& d);
 int gcorr_threads(const DevSys& d);
 int launch_gcorr(const DevSys& d, const void* coef, void* out, int kind, int mode, int q0, int nqc, long long vbase,
                  long long cells, int pf, void* stream);

@@ -430,13 +430,17 @@ const Variant* pick(const DevSys& d) {
 
 // The plane-wave correlation kernel (gcorr.cu) is variant kGcorrIndex; it is the default wherever it
 // is compiled for the system's band counts, and the FFT variants stay selectable.
-// Variant kGcorrPfIndex is the same kernel with the gather of the next G2 row software-pipelined.
-constexpr int kGcorrIndex = 64, kGcorrPfIndex = 65;
+// Variant kGcorrPfIndex is the same kernel with the gather of the next G2 row software-pipelined;
+// kGcorrSplitIndex runs the direct set with the vv' and cc' products of a block in separate CTAs
+// (the other sets as kGcorrIndex).
+constexpr int kGcorrIndex = 64, kGcorrPfIndex = 65, kGcorrSplitIndex = 66;
 constexpr int kGcorrDefaultPf = 0;
 bool use_gcorr(const DevSys& d) {
   if (!gcorr_valid(d)) return false;
-  return d.pair_variant == -1 || d.pair_variant == kGcorrIndex || d.pair_variant == kGcorrPfIndex;
+  return d.pair_variant == -1 || d.pair_variant == kGcorrIndex || d.pair_variant == kGcorrPfIndex ||
+         (d.pair_variant == kGcorrSplitIndex && gcorr_split_valid(d));
 }
+bool gcorr_split(const DevSys& d) { return d.pair_variant == kGcorrSplitIndex && gcorr_split_valid(d); }
 int gcorr_pf(const DevSys& d) {
   return d.pair_variant == kGcorrPfIndex ? 1 : d.pair_variant == kGcorrIndex ? 0 : kGcorrDefaultPf;
 }
@@ -481,14 +485,18 @@ size_t pair_ws_bytes(const DevSys& d) { return u_bytes(d) + (size_t)d.nkpt * d.n
 int pair_variants(const DevSys& d, int* out, int cap) {
   int n = 0;
   if (gcorr_valid(d)) {                      // rows = 0 marks the plane-wave correlation kernel
-    const int order[2] = {kGcorrDefaultPf ? kGcorrPfIndex : kGcorrIndex, kGcorrDefaultPf ? kGcorrIndex : kGcorrPfIndex};
+    const int order[3] = {kGcorrDefaultPf ? kGcorrPfIndex : kGcorrIndex, kGcorrDefaultPf ? kGcorrIndex : kGcorrPfIndex,
+                          kGcorrSplitIndex};
     for (int idx : order) {
+      if (idx == kGcorrSplitIndex && !gcorr_split_valid(d)) continue;
       if (out && n < cap) {
         int* o = out + 7 * n;
         o[0] = idx;
         o[1] = gcorr_threads(d);
         o[2] = 0;
-        o[3] = 2 * d.nv * d.nc > d.nv * d.nv + d.nc * d.nc ? 2 * d.nv * d.nc : d.nv * d.nv + d.nc * d.nc;
+        const int pd = idx == kGcorrSplitIndex ? (d.nv > d.nc ? d.nv * d.nv : d.nc * d.nc)
+                                               : d.nv * d.nv + d.nc * d.nc;     // direct-set products per CTA
+        o[3] = 2 * d.nv * d.nc > pd ? 2 * d.nv * d.nc : pd;
         o[4] = 2 * d.nb;
         o[5] = 1;
         o[6] = 1;
@@ -515,7 +523,7 @@ int pair_variants(const DevSys& d, int* out, int cap) {
 }
 
 int pair_variant_current(const DevSys& d) {
-  if (use_gcorr(d)) return gcorr_pf(d) ? kGcorrPfIndex : kGcorrIndex;
+  if (use_gcorr(d)) return gcorr_split(d) ? kGcorrSplitIndex : gcorr_pf(d) ? kGcorrPfIndex : kGcorrIndex;
   const Variant* v = pick(d);
   return v ? (int)(v - kVariants) : -1;
 }
@@ -550,8 +558,11 @@ static long long job_cells(const DevSys& d, int nqc, bool merged) {
 int launch_pair_direct(const DevSys& d, const void* u, void* rho_dir, int q_begin, int q_end, long long vbase,
                        int* status, void* stream) {
   if (use_gcorr(d))
-    return launch_gcorr(d, coef_copy(d, u), rho_dir, 1, 1, q_begin, q_end - q_begin, vbase,
-                        job_cells(d, q_end - q_begin, true), gcorr_pf(d), stream);
+    return gcorr_split(d)
+               ? launch_gcorr(d, coef_copy(d, u), rho_dir, 3, 1, q_begin, q_end - q_begin, vbase,
+                              job_cells(d, q_end - q_begin, false), 0, stream)
+               : launch_gcorr(d, coef_copy(d, u), rho_dir, 1, 1, q_begin, q_end - q_begin, vbase,
+                              job_cells(d, q_end - q_begin, true), gcorr_pf(d), stream);
   const Variant* v = pick(d);
   if (!v) return (int)cudaErrorInvalidValue;
   const size_t sm = v->pair_smem(d.ng_max);

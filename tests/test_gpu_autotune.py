@@ -66,7 +66,8 @@ def test_variants_bit_identical_and_match_oracle(bse, spec):
         rx = got[0][:, :g.shape[1]]
         assert np.abs(rx - g).max() / np.abs(g).max() < 1e-5, v        # exchange densities vs the oracle
         if v["rows"] == 0:
-            # the correlation kernels (plain and pipelined gather) run the same sums in the same order
+            # the correlation kernels (plain and pipelined gather, direct set merged or split over two CTAs)
+            # run the same sums in the same order
             if cref is None:
                 cref = got
             else:
@@ -91,7 +92,7 @@ def test_autotune_picks_fastest_and_caches(bse, tmp_path):
     s = generate(spec, wdtype=np.complex64)
     plan = bse.Plan([spec])
     variants, _ = bse.bse_pair_variants(plan, 0)
-    assert len(variants) == 5            # the correlation kernel (two gather schedules) and three FFT tile shapes
+    assert len(variants) == 6            # the correlation kernel (three schedules) and three FFT tile shapes
     F = Forward(plan, 0, nsteps=10, nw=50, qchunk=32)
     bse.bse_pair_densities(plan, 0, bse.BSE_PD_REALSPACE, _dev(s.coef, torch.complex64),
                            _dev(s.energies, torch.float64), None, None, None, 0, 0, F.ws_pair)
@@ -99,7 +100,7 @@ def test_autotune_picks_fastest_and_caches(bse, tmp_path):
     r = autotune.tune(plan, 0, F, reps=2, cache_path=cache)
     assert not r["cached"]
     ms = r["ms"]
-    assert len(ms) == 5 and all(t > 0 for t in ms.values())
+    assert len(ms) == 6 and all(t > 0 for t in ms.values())
     assert r["variant"]["index"] == int(min(ms, key=ms.get))
     assert bse.bse_pair_variants(plan, 0)[1] == r["variant"]["index"]
     stored = json.load(open(cache))
