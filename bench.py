@@ -190,8 +190,9 @@ class Step:
         bse.bse_build_kernel(plan, 0, bse.BSE_BK_INIT, F.rho_x, None, 0, 0, None, self.en, spec.delta, prec, F.H,
                              None)
         mark("exchange_kernel")
+        fdir = bse.BSE_PD_DIRECT | (bse.BSE_PD_TENSOR if self.tensor_pair(prec) else 0)
         for q0, q1 in F.chunks:
-            bse.bse_pair_densities(plan, 0, bse.BSE_PD_DIRECT, None, None, None, None, F.rho_dir, q0, q1, F.ws_pair)
+            bse.bse_pair_densities(plan, 0, fdir, None, None, None, None, F.rho_dir, q0, q1, F.ws_pair)
             mark("pair_direct")
             if w_ready is not None:
                 self.stream.wait_event(w_ready)
@@ -203,13 +204,21 @@ class Step:
         bse.bse_spectrum(plan, 0, F.H, F.P, spec.nsteps, self.om, spec.eta, F.eps2, F.ab, F.steps_done, F.ws_spec)
         mark("spectrum")
 
+    def tensor_pair(self, prec):
+        """The mixed step takes the direct pair densities on the tensor cores where the system has that route."""
+        from paper_1206_3518_gb300 import bse
+        return prec == bse.BSE_PREC_BF16X3 and bool(self.F.info["tensor_pair"])
+
     def kernels_per_step(self, prec):
         """Kernel launches of one step: realspace, exchange densities, dipole, K^x; per chunk the direct
-        densities and the direct term (FP32: W.rho GEMM + block kernel; BF16x3: two operand splits, the
-        tcgen05 GEMM and the block kernel); the Haydock kernel."""
+        densities (FP32: the correlation kernel; BF16x3: image packing, tile table and the tcgen05 kernel,
+        plus the FP64 G = 0 overlaps on the chunk holding q = 0) and the direct term (FP32: W.rho GEMM + block
+        kernel; BF16x3: two operand splits, the tcgen05 GEMM and the block kernel); the Haydock kernel."""
         from paper_1206_3518_gb300 import bse
-        per_chunk = 1 + (4 if prec == bse.BSE_PREC_BF16X3 else 2)
-        return 4 + per_chunk * len(self.F.chunks) + 1
+        mixed = prec == bse.BSE_PREC_BF16X3
+        pair = 3 if self.tensor_pair(prec) else 1
+        per_chunk = pair + (4 if mixed else 2)
+        return 4 + per_chunk * len(self.F.chunks) + (1 if self.tensor_pair(prec) else 0) + 1
 
 
 def stage_times(marks_per_step):
@@ -337,9 +346,10 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": msmx, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
         "config": dict(workload_config(spec, inf["ng_max"], qchunk, len(F.chunks)),
-                       precision="headline: BF16 hi/lo split-complex tcgen05 contractions (W.rho), FP32 "
-                                 "pair densities, K^x and block products, FP64 Lanczos coefficients and "
-                                 "continued fraction; compared with the all-FP32-contraction step",
+                       precision="headline: BF16 hi/lo split-complex tcgen05 contractions (direct pair "
+                                 "densities and W.rho), FP32 exchange densities, K^x and block products, FP64 "
+                                 "G = 0 overlaps, Lanczos coefficients and continued fraction; compared with "
+                                 "the all-FP32 step",
                        parallelism=f"replicas x{world}"),
         "stages_ms": stmx,
         "kernel_elements_per_s": kernel_only(msmx, stmx),
@@ -818,9 +828,11 @@ def run_stage(args):
         bse.bse_pair_densities(plan, 0, bse.BSE_PD_DIRECT, None, None, None, None, F.rho_dir, q0, q1, F.ws_pair)
         bse.bse_build_kernel(plan, 0, bse.BSE_BK_INIT, F.rho_x, None, 0, 0, None, en, spec.delta, prec, F.H, None)
 
+    fdir = bse.BSE_PD_DIRECT | (bse.BSE_PD_TENSOR if prec == bse.BSE_PREC_BF16X3 and F.info["tensor_pair"] else 0)
+
     def once():
         if args.only == "pair":
-            bse.bse_pair_densities(plan, 0, bse.BSE_PD_DIRECT, None, None, None, None, F.rho_dir, q0, q1, F.ws_pair)
+            bse.bse_pair_densities(plan, 0, fdir, None, None, None, None, F.rho_dir, q0, q1, F.ws_pair)
         elif args.only == "contract":
             bse.bse_build_kernel(plan, 0, bse.BSE_BK_DIRECT, None, F.rho_dir, q0, q1, W, None, spec.delta, prec, F.H,
                                  F.ws_kernel)
@@ -876,7 +888,8 @@ def pair_work(plan, spec, inf):
         ng = len(bse.bse_gvectors(plan, 0, q, 1))
         blk, _ = bse.bse_pair_blocks(plan, 0, q)
         cmac += ng * sum(npw[int(k2)] for _, k2 in blk)
-    return {"method": "correlation", "variant": current, "cmac": cmac * (spec.nv ** 2 + spec.nc ** 2)}
+    return {"method": "correlation", "variant": current, "cmac": cmac * (spec.nv ** 2 + spec.nc ** 2),
+            "tensor": bool(inf["tensor_pair"])}
 
 
 def _fp32_peak(peaks):
@@ -891,7 +904,18 @@ def stage_rooflines(st, spec, inf, peaks, src, nchunks, pw, prec):
     fp32 = _fp32_peak(peaks)
     out = {}
     ms = st["pair_direct"]
-    if pw["method"] == "correlation":
+    if prec != 0 and pw.get("tensor"):
+        useful = 24.0 * pw["cmac"]
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        out["pair_direct"] = {
+            "bound": "tensor", "kernel": "tcpair_kernel", "achieved": useful / (ms / 1e3) / 1e12, "peak": peak,
+            "unit": "TFLOP/s", "frac": useful / (ms / 1e3) / 1e12 / peak, "launches_per_step": 3 * nchunks + 1,
+            "work": "BF16x3 split-complex flops of the correlation itself: 3 hi/lo products x 8 real flops per "
+                    "complex multiply-add, sum over upper blocks of NG(q) |S(k')| (Nv^2 + Nc^2) (the padding of "
+                    "a tile's rows and K positions to the union of its spheres is not counted); the stage's "
+                    "whole time (image packing and tile table included)",
+            "traffic": None, "peak_source": src + " (sustained bf16: timed inside a long step)"}
+    elif pw["method"] == "correlation":
         flops = 8.0 * pw["cmac"]
         same = (GCORR_TRAFFIC["shape"] == (spec.lattice, spec.nv, spec.nc, spec.ecut)
                 and GCORR_TRAFFIC["sha1"] == _gcorr_sources_sha1())

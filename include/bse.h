@@ -86,6 +86,7 @@ typedef enum {
 #define BSE_PD_DIRECT    4u   /* A2 direct set rho_vv', rho_cc' of a q range   */
 #define BSE_PD_CHI0      8u   /* rho_vc^{k,k+q} for all k, q of a range (screening input) */
 #define BSE_PD_COUPLING 16u   /* rho_vc', rho_cv' of the upper blocks of a q range (coupling) */
+#define BSE_PD_TENSOR   32u   /* with DIRECT: the direct set on the tensor cores (BF16x3)      */
 #define BSE_BK_INIT      1u   /* A3 + A5 diagonal: H = diag + 2 K^x (upper)    */
 #define BSE_BK_DIRECT    2u   /* A4 + A5: H -= K^d for a q range, mirror       */
 #define BSE_BK_MIRROR    4u   /* A5 without A4: lower blocks and (B+B^H)/2      */
@@ -132,6 +133,9 @@ typedef struct {
   double prefactor;           /* C = 8 pi/(Omega Nk) */
   int kpoint_symmetry;        /* the system's bse_system.kpoint_symmetry */
   long long nfill;            /* upper blocks copied by BSE_BK_SYMFILL (0 without k-point symmetry) */
+  int tensor_pair;            /* 1: BSE_PD_TENSOR is available for this system */
+  int tc_region[3];           /* k' points per region of the tensor route (mesh axes 1-3) */
+  int tc_kpad;                /* K layout length of the tensor route (padded to 32) */
 } bse_info;
 
 typedef struct bse_plan bse_plan;
@@ -200,7 +204,18 @@ bse_status bse_rho_dir_count(const bse_plan* plan, int s, int q_begin, int q_end
  *          the same workspace.  Unused outputs may be NULL.  With BSE_PD_COUPLING (not with
  *          DIRECT or CHI0) rho_dir receives the coupling densities of bse_build_coupling,
  *          bse_rho_cpl_count(q_begin, q_end) vectors.
- * Errors: BSE_ERR_ARG (range, NULL for a requested output), BSE_ERR_WORKSPACE.
+ *          With BSE_PD_DIRECT | BSE_PD_TENSOR the direct set is computed on the tensor cores: for
+ *          each k, the blocks whose k' lie in one region of the k' mesh (bse_info.tc_region points)
+ *          form one GEMM per band n, D[G][(k', m)] = sum_{G2} conj(c_nk(G2 - G)) c_mk'(G2), rows G the
+ *          union of the blocks' q spheres, K the union of the region's spheres S(k'), operands split
+ *          hi + lo in BF16 with hi.hi + hi.lo + lo.hi accumulated in FP32 (relative error ~1e-5 of
+ *          the largest density instead of FP32 rounding); the G = 0 overlaps of the diagonal blocks
+ *          are summed in FP64.  Same layout and vectors as without the flag.  The precision of the
+ *          mixed build (bse_build_kernel with BSE_PREC_BF16X3); no counterpart in the paper, which
+ *          computes the densities by FFT.
+ * Errors: BSE_ERR_ARG (range, NULL for a requested output), BSE_ERR_WORKSPACE, BSE_ERR_UNSUPPORTED
+ *         (BSE_PD_TENSOR where bse_info.tensor_pair = 0), BSE_ERR_TIMEOUT (a tensor-route wait that
+ *         did not end within 2 s, through the status word).
  */
 bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags,
                               const void* coef, const double* energies,

@@ -23,7 +23,7 @@ BSE_PREC_FP32, BSE_PREC_BF16X3 = 0, 1
 BSE_WS_PAIR, BSE_WS_KERNEL, BSE_WS_SPECTRUM, BSE_WS_BACKWARD, BSE_WS_SCREEN = 0, 1, 2, 3, 4
 BSE_WS_COUPLING, BSE_WS_COUPLED, BSE_WS_RITZ = 5, 6, 7
 BSE_WS_CHI0, BSE_WS_ALDA, BSE_WS_EPSM, BSE_WS_STATES = 8, 9, 10, 11
-BSE_PD_REALSPACE, BSE_PD_EXCHANGE, BSE_PD_DIRECT, BSE_PD_CHI0, BSE_PD_COUPLING = 1, 2, 4, 8, 16
+BSE_PD_REALSPACE, BSE_PD_EXCHANGE, BSE_PD_DIRECT, BSE_PD_CHI0, BSE_PD_COUPLING, BSE_PD_TENSOR = 1, 2, 4, 8, 16, 32
 BSE_BK_INIT, BSE_BK_DIRECT, BSE_BK_MIRROR, BSE_BK_SYMFILL = 1, 2, 4, 8
 BSE_BC_INIT, BSE_BC_DIRECT, BSE_BC_MIRROR = 1, 2, 4
 
@@ -49,7 +49,8 @@ class BseInfo(ctypes.Structure):
                 ("npw_max", ctypes.c_int), ("ng_max", ctypes.c_int), ("ng0", ctypes.c_int),
                 ("nq", ctypes.c_int), ("nblocks", ctypes.c_longlong), ("omega_cell", ctypes.c_double),
                 ("norm", ctypes.c_double), ("prefactor", ctypes.c_double), ("kpoint_symmetry", ctypes.c_int),
-                ("nfill", ctypes.c_longlong)]
+                ("nfill", ctypes.c_longlong), ("tensor_pair", ctypes.c_int), ("tc_region", ctypes.c_int * 3),
+                ("tc_kpad", ctypes.c_int)]
 
 
 class BsePairVariant(ctypes.Structure):
@@ -187,7 +188,9 @@ class Plan:
     def info(self, s=0) -> dict:
         inf = BseInfo()
         _check(load().bse_plan_info(self.handle, s, ctypes.byref(inf)))
-        return {f: getattr(inf, f) for f, _ in BseInfo._fields_}
+        out = {f: getattr(inf, f) for f, _ in BseInfo._fields_}
+        out["tc_region"] = tuple(inf.tc_region)
+        return out
 
 
 def bse_plan_create(specs) -> Plan:

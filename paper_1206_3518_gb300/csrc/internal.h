@@ -41,6 +41,14 @@ struct DevSys {
   // stored as -(rep ik2 + 1) when the block is the representative's Hermitian mirror
   const int4* fill;
   long long nfill;
+  // Tensor-core direct densities (tcpair.cu).  The k' mesh is cut into regions of tc_rg[0] x tc_rg[1] x
+  // tc_rg[2] points (tc_nr regions per axis, tc_rsize points each); region r has a K layout, the union of
+  // the spheres of its k' in lexicographic order (tc_kcount[r] entries, padded to tc_kpad).
+  int tc_rg[3], tc_nr[3], tc_nreg, tc_rsize, tc_kpad;
+  const char4* tc_klist;          // [tc_nreg][tc_kpad] G of each K position
+  const int* tc_kcount;           // [tc_nreg]
+  const short* tc_kpos;           // [nkpt][npw_max] K position of sphere point i of k in its region's layout
+  const short* tc_pmap;           // [nq][(2 fwf0 + 1)(2 fwf1 + 1)(2 fwf2 + 1)] sphere position of g on q, -1 if absent
 };
 
 struct SysPlan {
@@ -83,6 +91,12 @@ int launch_screening(const DevSys& d, void* rho_chi, const double* energies, con
 int pair_supported(const DevSys& d);
 size_t pair_ws_bytes(const DevSys& d);
 int gcorr_valid(const DevSys& d);
+int tcpair_valid(const DevSys& d);
+size_t tcpair_ws_bytes(const DevSys& d);
+int launch_tcpair(const DevSys& d, const void* coef, void* ws, void* rho_dir, int q_begin, int q_end,
+                  long long vbase, int* status, void* stream);
+int launch_pair_direct_tensor(const DevSys& d, void* ws, void* rho_dir, int q_begin, int q_end, long long vbase,
+                              int* status, void* stream);
 int gcorr_split_valid(const DevSys& d);
 int gcorr_threads(const DevSys& d);
 int launch_gcorr(const DevSys& d, const void* coef, void* out, int kind, int mode, int q0, int nqc, long long vbase,

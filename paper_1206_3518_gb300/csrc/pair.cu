@@ -480,7 +480,18 @@ int upload_twiddles() {
 
 int pair_supported(const DevSys& d) { return pick(d) != nullptr; }
 
-size_t pair_ws_bytes(const DevSys& d) { return u_bytes(d) + (size_t)d.nkpt * d.nb * d.npw_max * 8; }
+static size_t pair_base_bytes(const DevSys& d) {
+  return (u_bytes(d) + (size_t)d.nkpt * d.nb * d.npw_max * 8 + 255) & ~(size_t)255;
+}
+
+// u(r), the coefficient copy, then the tensor route's packed images and tile table (when valid).
+size_t pair_ws_bytes(const DevSys& d) { return pair_base_bytes(d) + tcpair_ws_bytes(d); }
+
+int launch_pair_direct_tensor(const DevSys& d, void* ws, void* rho_dir, int q_begin, int q_end, long long vbase,
+                              int* status, void* stream) {
+  return launch_tcpair(d, coef_copy(d, ws), (char*)ws + pair_base_bytes(d), rho_dir, q_begin, q_end, vbase, status,
+                       stream);
+}
 
 int pair_variants(const DevSys& d, int* out, int cap) {
   int n = 0;

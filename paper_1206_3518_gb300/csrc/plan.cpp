@@ -444,6 +444,86 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
     }
   }
 
+  // ---- tensor-core direct densities: k' regions, their K layouts, sphere positions ----
+  // Regions hold at most 128 / max(Nv, Nc) mesh points (one MMA N tile of (k', band) columns).  When a
+  // plane of the mesh holds that many, regions are one plane thick in k'_1 (the q chunks are ranges of
+  // q, i.e. slabs in q_1); the divisors of the mesh with the largest product are taken, then the most
+  // compact (smallest largest extent n_j / nk_j).
+  std::vector<char4> h_klist;
+  std::vector<int> h_kcount;
+  std::vector<short> h_kpos((size_t)nkpt * npw_max, 0), h_pmap;
+  {
+    const int rmax = 128 / std::max(s.nv, s.nc);
+    const bool thin = nk2 * nk3 >= rmax;
+    int best[3] = {1, 1, 1};
+    long long best_p = 0;
+    double best_e = 1e30;
+    for (int r1 = 1; r1 <= nk1; ++r1)
+      for (int r2 = 1; r2 <= nk2; ++r2)
+        for (int r3 = 1; r3 <= nk3; ++r3) {
+          if (nk1 % r1 || nk2 % r2 || nk3 % r3) continue;
+          if (thin && r1 != 1) continue;
+          const long long pr = (long long)r1 * r2 * r3;
+          if (pr > rmax) continue;
+          const double e = std::max({(double)r1 / nk1, (double)r2 / nk2, (double)r3 / nk3});
+          if (pr > best_p || (pr == best_p && e < best_e - 1e-12)) {
+            best_p = pr;
+            best_e = e;
+            best[0] = r1;
+            best[1] = r2;
+            best[2] = r3;
+          }
+        }
+    for (int j = 0; j < 3; ++j) {
+      d.tc_rg[j] = best[j];
+      d.tc_nr[j] = s.nk[j] / best[j];
+    }
+    d.tc_nreg = d.tc_nr[0] * d.tc_nr[1] * d.tc_nr[2];
+    d.tc_rsize = best[0] * best[1] * best[2];
+    std::vector<std::vector<std::array<int, 3>>> lists(d.tc_nreg);
+    for (int ik = 0; ik < nkpt; ++ik) {
+      int o[3];
+      offs(ik, o);
+      const int r = ((o[0] / best[0]) * d.tc_nr[1] + o[1] / best[1]) * d.tc_nr[2] + o[2] / best[2];
+      const auto& g = sp.gk[ik];
+      for (int t = 0; t < (int)g.size() / 3; ++t) lists[r].push_back({g[3 * t], g[3 * t + 1], g[3 * t + 2]});
+    }
+    int kmax = 0;
+    for (auto& l : lists) {
+      std::sort(l.begin(), l.end());
+      l.erase(std::unique(l.begin(), l.end()), l.end());
+      kmax = std::max(kmax, (int)l.size());
+    }
+    d.tc_kpad = (kmax + 31) / 32 * 32;
+    h_klist.assign((size_t)d.tc_nreg * d.tc_kpad, make_char4(0, 0, 0, 1));   // w = 1: padding
+    h_kcount.assign(d.tc_nreg, 0);
+    for (int r = 0; r < d.tc_nreg; ++r) {
+      h_kcount[r] = (int)lists[r].size();
+      for (size_t t = 0; t < lists[r].size(); ++t)
+        h_klist[(size_t)r * d.tc_kpad + t] =
+            make_char4((signed char)lists[r][t][0], (signed char)lists[r][t][1], (signed char)lists[r][t][2], 0);
+    }
+    for (int ik = 0; ik < nkpt; ++ik) {
+      int o[3];
+      offs(ik, o);
+      const int r = ((o[0] / best[0]) * d.tc_nr[1] + o[1] / best[1]) * d.tc_nr[2] + o[2] / best[2];
+      const auto& g = sp.gk[ik];
+      for (int t = 0; t < (int)g.size() / 3; ++t) {
+        const std::array<int, 3> key = {g[3 * t], g[3 * t + 1], g[3 * t + 2]};
+        const auto it = std::lower_bound(lists[r].begin(), lists[r].end(), key);
+        h_kpos[(size_t)ik * npw_max + t] = (short)(it - lists[r].begin());
+      }
+    }
+    const int p0 = 2 * d.fwf[0] + 1, p1 = 2 * d.fwf[1] + 1, p2 = 2 * d.fwf[2] + 1;
+    h_pmap.assign((size_t)nkpt * p0 * p1 * p2, (short)-1);
+    for (int iq = 0; iq < nkpt; ++iq) {
+      const auto& g = sp.gq[iq];
+      for (int t = 0; t < (int)g.size() / 3; ++t)
+        h_pmap[(size_t)iq * p0 * p1 * p2 + ((size_t)(g[3 * t] + d.fwf[0]) * p1 + g[3 * t + 1] + d.fwf[1]) * p2 +
+               g[3 * t + 2] + d.fwf[2]] = (short)t;
+    }
+  }
+
   if (!device) return BSE_OK;
   size_t off = 0;
   const size_t o_gk = off; off = align256(off + h_gk.size() * sizeof(char4));
@@ -462,6 +542,10 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   const size_t o_qp = off; off = align256(off + sp.qperm.size() * sizeof(int));
   const size_t o_qs = off; off = align256(off + h_qsym.size() * sizeof(int2));
   const size_t o_fill = off; off = align256(off + (sp.fill.empty() ? 1 : sp.fill.size()) * sizeof(int4));
+  const size_t o_tkl = off; off = align256(off + h_klist.size() * sizeof(char4));
+  const size_t o_tkc = off; off = align256(off + h_kcount.size() * sizeof(int));
+  const size_t o_tkp = off; off = align256(off + h_kpos.size() * sizeof(short));
+  const size_t o_tpm = off; off = align256(off + h_pmap.size() * sizeof(short));
   char* base = nullptr;
   bse_status st = cuda_check(cudaMalloc((void**)&base, off), "cudaMalloc(plan tables)");
   if (st != BSE_OK) return st;
@@ -483,6 +567,10 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   if (!err) err = up(o_qp, sp.qperm.data(), sp.qperm.size() * sizeof(int));
   if (!err) err = up(o_qs, h_qsym.data(), h_qsym.size() * sizeof(int2));
   if (!err) err = up(o_fill, sp.fill.data(), sp.fill.size() * sizeof(int4));
+  if (!err) err = up(o_tkl, h_klist.data(), h_klist.size() * sizeof(char4));
+  if (!err) err = up(o_tkc, h_kcount.data(), h_kcount.size() * sizeof(int));
+  if (!err) err = up(o_tkp, h_kpos.data(), h_kpos.size() * sizeof(short));
+  if (!err) err = up(o_tpm, h_pmap.data(), h_pmap.size() * sizeof(short));
   if ((st = cuda_check(err, "cudaMemcpy(plan tables)")) != BSE_OK) return st;
   d.gk = (const char4*)(base + o_gk);
   d.npw = (const int*)(base + o_npw);
@@ -499,6 +587,10 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   d.qperm = (const int*)(base + o_qp);
   d.qsym = (const int2*)(base + o_qs);
   d.fill = (const int4*)(base + o_fill);
+  d.tc_klist = (const char4*)(base + o_tkl);
+  d.tc_kcount = (const int*)(base + o_tkc);
+  d.tc_kpos = (const short*)(base + o_tkp);
+  d.tc_pmap = (const short*)(base + o_tpm);
   return BSE_OK;
 }
 
@@ -584,6 +676,9 @@ bse_status bse_plan_info(const bse_plan* plan, int s, bse_info* info) {
   info->prefactor = d.prefactor;
   info->kpoint_symmetry = plan->sys[s].sys.kpoint_symmetry ? 1 : 0;
   info->nfill = d.nfill;
+  info->tensor_pair = tcpair_valid(d);
+  for (int j = 0; j < 3; ++j) info->tc_region[j] = d.tc_rg[j];
+  info->tc_kpad = d.tc_kpad;
   return BSE_OK;
 }
 
@@ -727,7 +822,13 @@ bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags, const void*
   if (flags & BSE_PD_DIRECT) {
     if (!rho_dir || q_begin < 0 || q_end > d.nq || q_begin >= q_end) return set_error(BSE_ERR_ARG, "bad direct range");
     const long long vb = sp.qvec_off[q_begin];
-    if ((st = cuda_check(launch_pair_direct(d, ws, rho_dir, q_begin, q_end, vb, plan->d_status, stream), "pair direct")) != BSE_OK)
+    if (flags & BSE_PD_TENSOR) {
+      if (!tcpair_valid(d)) return set_error(BSE_ERR_UNSUPPORTED, "no tensor-core route for this system");
+      if ((st = cuda_check(launch_pair_direct_tensor(d, ws, rho_dir, q_begin, q_end, vb, plan->d_status, stream),
+                           "pair direct (tensor)")) != BSE_OK)
+        return st;
+    } else if ((st = cuda_check(launch_pair_direct(d, ws, rho_dir, q_begin, q_end, vb, plan->d_status, stream),
+                                "pair direct")) != BSE_OK)
       return st;
   }
   return BSE_OK;

@@ -27,6 +27,7 @@
 
 #include "internal.h"
 #include "layout.cuh"
+#include "umma.cuh"
 
 namespace bse {
 namespace {
@@ -42,68 +43,17 @@ constexpr int kStage = 2 * kTileA + 2 * NMAX * kRow;   // A hi, A lo, B hi, B lo
 constexpr int kAccCols = 256;                // one accumulator: Re in columns [0,128), Im in [128,256)
 constexpr size_t kTcSmem = (size_t)kStages * kStage + 1024 + 256;   // ring, 1 KB alignment slack, barriers
 
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-// Bounded wait on an mbarrier phase; false after 2 s.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  const unsigned long long t0 = gtimer();
-  while (true) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (gtimer() - t0 > 2000000000ull) return false;
-  }
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// UMMA shared-memory descriptor: K-major, 128B swizzle, 8-row atoms 1024 B apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);          // start address
-  d |= (uint64_t)1 << 16;                           // leading-dimension byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;                 // stride-dimension byte offset
-  d |= (uint64_t)1 << 46;                           // descriptor version (sm_100 family)
-  d |= (uint64_t)2 << 61;                           // 128B swizzle
-  return d;
-}
-
-// Instruction descriptor: D f32, A/B bf16, both K-major, M = 128, N = n; bit 13 negates A.
-__host__ __device__ constexpr uint32_t idesc_of(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-}
-constexpr uint32_t kNegA = 1u << 13;
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(da), "l"(db), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// 16-byte chunk c of row r of a swizzled K-major tile (rows of 128 bytes).
-__device__ __forceinline__ uint32_t swz(int r, int c) { return (uint32_t)(r * kRow + ((c ^ (r & 7)) << 4)); }
+using umma::gtimer;
+using umma::idesc_of;
+using umma::kNegA;
+using umma::mbar_arrive;
+using umma::mbar_init;
+using umma::mbar_wait;
+using umma::mma_bf16;
+using umma::mma_commit;
+using umma::smem_desc;
+using umma::smem_u32;
+using umma::swz;
 
 __device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
   __nv_bfloat162 h[4], l[4];

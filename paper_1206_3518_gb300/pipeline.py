@@ -45,15 +45,22 @@ class Forward:
         self.ab = torch.zeros(2 * nsteps, dtype=torch.float64, device=dev)
         self.steps_done = torch.zeros(1, dtype=torch.int32, device=dev)
 
-    def build(self, coef, energies, W, delta, prec=bse.BSE_PREC_FP32):
-        """A1-A6: pair densities, dipole and H (direct term streamed over q chunks)."""
+    def build(self, coef, energies, W, delta, prec=bse.BSE_PREC_FP32, tensor_pair=None):
+        """A1-A6: pair densities, dipole and H (direct term streamed over q chunks).
+
+        tensor_pair: direct pair densities on the tensor cores (BSE_PD_TENSOR); by default with the
+        mixed precision where the system has that route.
+        """
         p, s = self.plan, self.s
+        if tensor_pair is None:
+            tensor_pair = prec == bse.BSE_PREC_BF16X3 and bool(self.info["tensor_pair"])
+        fdir = bse.BSE_PD_DIRECT | (bse.BSE_PD_TENSOR if tensor_pair else 0)
         bse.bse_pair_densities(p, s, bse.BSE_PD_REALSPACE | bse.BSE_PD_EXCHANGE, coef, energies, self.rho_x, self.P,
                                None, 0, 0, self.ws_pair)
         bse.bse_build_kernel(p, s, bse.BSE_BK_INIT, self.rho_x, None, 0, 0, None, energies, delta, prec, self.H,
                              None)
         for q0, q1 in self.chunks:
-            bse.bse_pair_densities(p, s, bse.BSE_PD_DIRECT, None, None, None, None, self.rho_dir, q0, q1, self.ws_pair)
+            bse.bse_pair_densities(p, s, fdir, None, None, None, None, self.rho_dir, q0, q1, self.ws_pair)
             bse.bse_build_kernel(p, s, bse.BSE_BK_DIRECT, None, self.rho_dir, q0, q1, W, None, delta, prec, self.H,
                                  self.ws_kernel)
         if self.info["kpoint_symmetry"]:
