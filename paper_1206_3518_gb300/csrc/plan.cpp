@@ -445,7 +445,8 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   }
 
   // ---- tensor-core direct densities: k' regions, their K layouts, sphere positions ----
-  // Regions hold at most 128 / max(Nv, Nc) mesh points (one MMA N tile of (k', band) columns).  When a
+  // Regions hold at most 96 / max(Nv, Nc) mesh points (one MMA N tile of (k', band) columns, at most 96 so
+  // that two accumulators and two A tiles fit in tensor memory).  When a
   // plane of the mesh holds that many, regions are one plane thick in k'_1 (the q chunks are ranges of
   // q, i.e. slabs in q_1); the divisors of the mesh with the largest product are taken, then the most
   // compact (smallest largest extent n_j / nk_j).
@@ -453,7 +454,7 @@ bse_status build_system(const bse_system& in, SysPlan& sp, bool device) {
   std::vector<int> h_kcount;
   std::vector<short> h_kpos((size_t)nkpt * npw_max, 0), h_pmap;
   {
-    const int rmax = 128 / std::max(s.nv, s.nc);
+    const int rmax = 96 / std::max(s.nv, s.nc);
     const bool thin = nk2 * nk3 >= rmax;
     int best[3] = {1, 1, 1};
     long long best_p = 0;

@@ -15,8 +15,8 @@
 //   columns    the tile's blocks times the bands m of the set.
 //
 // A_n is gathered into shared memory from a dense index box of S(k) (points outside S(k) read a zero
-// row); B comes from packed images of the coefficients in each region's K layout (zero off S(k')),
-// written once per call, each block's bands as one group of rows in the eight 128B-swizzle phases.  The epilogue keeps, for every block, the rows on its own sphere and writes
+// row); B comes from packed panels of the coefficients of each region's points in its K layout (zero off
+// S(k')), written once per call.  The epilogue keeps, for every block, the rows on its own sphere and writes
 // them at their sphere positions, so the output is the direct set of the correlation kernels.
 //
 // Arithmetic (BF16x3): every operand is split x = hi + lo in BF16 and each real product accumulates
@@ -24,12 +24,14 @@
 // W.rho products of the mixed build).  The G = 0 overlaps of the diagonal blocks (k' = k), which
 // meet the q = 0 head of W, are summed again in FP64 afterwards (tcpair_diag_kernel).
 //
-// tcpair_kernel is persistent (one CTA per SM) and takes tiles (k, region) from a counter.  Warps 0-3
-// drain the accumulators, warp 4 issues the MMAs (12 per 16 complex K), warps 5-12 gather the A tile of
-// each K chunk (32 complex K values) into a ring of shared-memory stages, and warp 13 brings the B rows
-// with bulk copies (two per block: its hi rows and its lo rows, counted on the stage's mbarrier).  Two accumulators
-// (Re | Im, 256 TMEM columns each) alternate between passes (one band n, 128 rows), so the epilogue
-// of one pass overlaps the MMAs of the next.  Every mbarrier wait is bounded (2 s); on expiry the CTA
+// tcpair_kernel is persistent (one CTA per SM) and takes tiles (k, region) from a counter, region-major.
+// Warps 0-3 drain the accumulators, warp 4 issues the MMAs (12 per 16 complex K, A from tensor memory,
+// B from shared memory), warps 5-12 gather the A tile of each K chunk (32 complex K values) straight into
+// tensor memory (two A slots, tcgen05.st), and warp 13 brings the B rows into a ring of shared-memory
+// stages with bulk copies (the region's panel of the chunk: its hi rows and its lo rows, counted on the
+// stage's mbarrier); the columns of a region's points without a block in the tile are computed and dropped.
+// Two accumulators (Re | Im, 2 N <= 192 TMEM columns each) alternate between passes (one band n, 128
+// rows), so the epilogue of one pass overlaps the MMAs of the next.  Every mbarrier wait is bounded (2 s); on expiry the CTA
 // records BSE_ERR_TIMEOUT, stops issuing, waits (bounded) for its MMAs in flight, frees its tensor
 // memory and returns.
 #include <cuda_bf16.h>
@@ -55,16 +57,13 @@ constexpr int kMmaWarp = 4;
 constexpr int kG0 = 5;                         // first gather warp
 constexpr int kGWarps = 8;
 constexpr int kB0 = kG0 + kGWarps;             // the B producer warp (bulk copies)
-constexpr int kMaxStages = 3;
+constexpr int kMaxStages = 6;                  // B ring depth at most
+constexpr int kAStages = 2;                    // A tiles in tensor memory
 constexpr int kThreads = (kB0 + 1) * 32;
 constexpr int kGThreads = kGWarps * 32;
 constexpr int kTKC = 32;                       // complex K values per stage
-constexpr int kTile = 128 * umma::kRow;        // one split of a 128-row tile (16 KB)
-constexpr int kAcc = 256;                      // one accumulator: Re in columns [0,128), Im in [128,256)
+constexpr int kACols = 64;                     // one A tile in TMEM: two K16 halves x (Re hi, Im hi, Re lo, Im lo) x 8
 constexpr int kImgRow = 256;                   // packed image of 32 K values: hi row (128 B), lo row (128 B)
-// Packed images, per k': for the set of the valence bands (nv rows), then of the conduction bands (nc rows),
-// per K chunk c and swizzle variant v (0..7), one group of rows [hi rows | lo rows] (128 bytes each).
-
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct TpGeo {
@@ -85,7 +84,7 @@ TpGeo tp_geo(const DevSys& d, int stages) {
   g.nkc = d.tc_kpad / kTKC;
   const int mb = d.nv > d.nc ? d.nv : d.nc;
   g.nmax = (d.tc_rsize * mb + 15) / 16 * 16;
-  g.stage_bytes = 2 * kTile + 2 * g.nmax * umma::kRow;
+  g.stage_bytes = 2 * g.nmax * umma::kRow;      // B hi rows, B lo rows
   const int rx = d.fwf[0] + d.fpair[0], ry = d.fwf[1] + d.fpair[1], rz = d.fwf[2] + d.fpair[2];
   g.bx = 2 * rx + 1;
   g.by = 2 * ry + 1;
@@ -95,7 +94,7 @@ TpGeo tp_geo(const DevSys& d, int stages) {
   g.rowbox = (2 * d.fpair[0] + 1) * (2 * d.fpair[1] + 1) * (2 * d.fpair[2] + 1);
   g.nwords = (g.rowbox + 31) / 32;
   size_t o = (size_t)stages * g.stage_bytes;
-  g.o_bar = (int)o; o += align16((size_t)(2 * stages + 5) * 8 + 8 * sizeof(int));
+  g.o_bar = (int)o; o += align16((size_t)(2 * stages + 2 * kAStages + 5) * 8 + 8 * sizeof(int));
   g.o_bbox = (int)o; o += align16((size_t)g.bbox_n * 2);
   g.o_kcoef = (int)o; o += align16((size_t)(d.npw_max + 1) * 8);
   g.o_kkey = (int)o; o += align16((size_t)d.tc_kpad * 4);
@@ -129,16 +128,22 @@ __device__ __forceinline__ uint32_t split_word(float x) {
   return (uint32_t)*reinterpret_cast<const unsigned short*>(&h) | (bf16_bits(r) << 16);
 }
 
-// ---------------------------------------------------------------- packed coefficient images
-// Group (k', set, c, v): the set's bands as consecutive rows, [Re 32 | Im 32] in the region's K layout
-// (zero off S(k')), with the 16-byte chunks of band row m permuted for a tile row r = r0 + m, r0 mod 8 = v
-// (128B swizzle), so two bulk copies (hi rows, lo rows) land a block's columns of a B tile as the MMA reads
-// them.
-__device__ __forceinline__ size_t group_off(const DevSys& d, int k2, int set, int c, int v, int nkc) {
-  const size_t per_k = (size_t)nkc * 8 * 2 * umma::kRow * (d.nv + d.nc);
-  const size_t set_off = set ? (size_t)nkc * 8 * 2 * umma::kRow * d.nv : 0;
+// ---------------------------------------------------------------- packed coefficient panels
+// Packed B panels: for each region r, set (valence bands, then conduction bands) and K chunk c, the rows
+// j = slot nset + m of every k' of the region (slot: its position in the region, m: its band in the set),
+// [Re 32 | Im 32] BF16 in the region's K layout (zero off S(k')), hi rows then lo rows, the 16-byte chunks of
+// row j permuted by j mod 8 (128B swizzle): a stage's B tile is two bulk copies.
+__device__ __forceinline__ size_t panel_off(const DevSys& d, int r, int set, int c, int nkc) {
+  const size_t per_r = (size_t)nkc * 2 * umma::kRow * d.tc_rsize * (d.nv + d.nc);
+  const size_t set_off = set ? (size_t)nkc * 2 * umma::kRow * d.tc_rsize * d.nv : 0;
   const int nset = set ? d.nc : d.nv;
-  return (size_t)k2 * per_k + set_off + ((size_t)c * 8 + v) * 2 * umma::kRow * nset;
+  return (size_t)r * per_r + set_off + (size_t)c * 2 * umma::kRow * d.tc_rsize * nset;
+}
+
+__device__ __forceinline__ void region_of(const DevSys& d, int k2, int& r, int& slot) {
+  const int o0 = k2 / (d.nk2 * d.nk3), o1 = (k2 / d.nk3) % d.nk2, o2 = k2 % d.nk3;
+  r = ((o0 / d.tc_rg[0]) * d.tc_nr[1] + o1 / d.tc_rg[1]) * d.tc_nr[2] + o2 / d.tc_rg[2];
+  slot = ((o0 % d.tc_rg[0]) * d.tc_rg[1] + o1 % d.tc_rg[1]) * d.tc_rg[2] + o2 % d.tc_rg[2];
 }
 
 __global__ void tcpair_pack_kernel(DevSys d, const float2* __restrict__ coef, unsigned char* __restrict__ bimg,
@@ -151,21 +156,19 @@ __global__ void tcpair_pack_kernel(DevSys d, const float2* __restrict__ coef, un
   const int k2 = (int)(kb / d.nb), band = (int)(kb - (long long)k2 * d.nb);
   if (i >= d.npw[k2]) return;
   const int set = band < d.nv ? 0 : 1, m = set ? band - d.nv : band, nset = set ? d.nc : d.nv;
+  int r, slot;
+  region_of(d, k2, r, slot);
   const int l = d.tc_kpos[(size_t)k2 * d.npw_max + i];
   const float2 c = coef[t];
   const uint32_t re = split_word(c.x), im = split_word(c.y);
-  const int e = l % kTKC;
-#pragma unroll
-  for (int v = 0; v < 8; ++v) {
-    unsigned short* hi = reinterpret_cast<unsigned short*>(bimg + group_off(d, k2, set, l / kTKC, v, nkc)) + m * 64;
-    unsigned short* lo = hi + nset * 64;
-    const int ph = (v + m) & 7;
-    const int cr = ((e >> 3) ^ ph) * 8 + (e & 7), ci = ((4 + (e >> 3)) ^ ph) * 8 + (e & 7);
-    hi[cr] = (unsigned short)(re & 0xFFFFu);
-    hi[ci] = (unsigned short)(im & 0xFFFFu);
-    lo[cr] = (unsigned short)(re >> 16);
-    lo[ci] = (unsigned short)(im >> 16);
-  }
+  const int e = l % kTKC, j = slot * nset + m, ph = j & 7;
+  unsigned short* hi = reinterpret_cast<unsigned short*>(bimg + panel_off(d, r, set, l / kTKC, nkc)) + j * 64;
+  unsigned short* lo = hi + d.tc_rsize * nset * 64;
+  const int cr = ((e >> 3) ^ ph) * 8 + (e & 7), ci = ((4 + (e >> 3)) ^ ph) * 8 + (e & 7);
+  hi[cr] = (unsigned short)(re & 0xFFFFu);
+  hi[ci] = (unsigned short)(im & 0xFFFFu);
+  lo[cr] = (unsigned short)(re >> 16);
+  lo[ci] = (unsigned short)(im >> 16);
 }
 
 // ---------------------------------------------------------------- tile table of a q range
@@ -176,10 +179,8 @@ __global__ void tcpair_tiles_kernel(DevSys d, int q_begin, int nqc, int* __restr
   const int q = q_begin + (int)(t / d.nkpt), k = (int)(t % d.nkpt);
   const int b = d.blkidx[(size_t)q * d.nkpt + k];
   if (b < 0) return;
-  const int k2 = d.blocks[b].y;
-  const int o0 = k2 / (d.nk2 * d.nk3), o1 = (k2 / d.nk3) % d.nk2, o2 = k2 % d.nk3;
-  const int r = ((o0 / d.tc_rg[0]) * d.tc_nr[1] + o1 / d.tc_rg[1]) * d.tc_nr[2] + o2 / d.tc_rg[2];
-  const int s = ((o0 % d.tc_rg[0]) * d.tc_rg[1] + o1 % d.tc_rg[1]) * d.tc_rg[2] + o2 % d.tc_rg[2];
+  int r, s;
+  region_of(d, d.blocks[b].y, r, s);
   blist[((size_t)k * d.tc_nreg + r) * d.tc_rsize + s] = b;
 }
 
@@ -190,9 +191,11 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
                                                              float2* __restrict__ out, TpGeo g, int* status) {
   extern __shared__ __align__(1024) unsigned char tp_smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)tp_smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(sm + g.o_bar);     // [stages] gathered
-  uint64_t* empty = full + g.stages;               // [stages] MMAs done with the stage
-  uint64_t* tfull = empty + g.stages;              // [2] accumulator complete
+  uint64_t* full_b = (uint64_t*)(sm + g.o_bar);   // [stages] B rows landed
+  uint64_t* empty_b = full_b + g.stages;          // [stages] MMAs done with the B stage
+  uint64_t* full_a = empty_b + g.stages;          // [2] A tile written to tensor memory
+  uint64_t* empty_a = full_a + kAStages;          // [2] MMAs done with the A tile
+  uint64_t* tfull = empty_a + kAStages;           // [2] accumulator complete
   uint64_t* tempty = tfull + 2;                    // [2] accumulator drained
   uint64_t* drain = tempty + 2;                    // every MMA of this CTA complete
   int* iv = (int*)(drain + 1);                     // tmem, fail, tile, nblk, rows, k of the box
@@ -215,17 +218,23 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
   const int p0 = d.fpair[0], p1 = d.fpair[1], p2 = d.fpair[2];
   const int rb1 = 2 * p1 + 1, rb2 = 2 * p2 + 1;
   const int nv = d.nv, nc = d.nc;
+  const uint32_t half = (uint32_t)((g.nmax + 31) & ~31);    // Re [0, half), Im [half, 2 half) of an accumulator
+  const uint32_t acc_cols = 2 * half;
+  const uint32_t a_col0 = 2 * acc_cols;                      // the A tiles after the two accumulators
 
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(iv)),
-                 "r"(2 * kAcc)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(iv)), "r"(512)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 32) {
     for (int i = 0; i < g.stages; ++i) {
-      mbar_init(smem_u32(full + i), kGWarps + 1);
-      mbar_init(smem_u32(empty + i), 1);
+      mbar_init(smem_u32(full_b + i), 1);
+      mbar_init(smem_u32(empty_b + i), 1);
+    }
+    for (int i = 0; i < kAStages; ++i) {
+      mbar_init(smem_u32(full_a + i), kGWarps);
+      mbar_init(smem_u32(empty_a + i), 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(tfull + i), 1);
@@ -289,8 +298,12 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
     if (tid == 0) iv[5] = k;
     const int nblk = iv[3];
     if (nblk == 0) continue;
-    for (int i = tid; i < nblk; i += kThreads) {
-      const int b = cols[i];
+    for (int i = tid; i < rs; i += kThreads) {  // per slot of the region; x = -1: no block of this range
+      const int b = slot[i];
+      if (b < 0) {
+        binfo[i] = make_int4(-1, 0, 0, 0);
+        continue;
+      }
       const int4 blk = d.blocks[b];
       const long long qb = d.qblk_off[blk.z], nbq = d.qblk_off[blk.z + 1] - qb;
       const long long base = d.qvec_off[blk.z] - g.vbase;
@@ -311,7 +324,8 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
     __syncthreads();
     int ng_ref;
     {
-      const int4 bi = binfo[0];
+      const int4 b0 = d.blocks[cols[0]];
+      const int4 bi = make_int4(b0.z, b0.y, b0.w, 0);
       const int gx = (bi.z & 3) - 1, gy = ((bi.z >> 2) & 3) - 1, gz = ((bi.z >> 4) & 3) - 1;
       ng_ref = d.ngq[bi.x];
       for (int p = tid; p < ng_ref; p += kThreads) {
@@ -351,8 +365,9 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
     const int nmt = (MT + 127) / 128;
     const int nch = (kc + kTKC - 1) / kTKC;
 
-    if (warp >= kG0 && warp < kB0) {             // ---- gather: A tile of each K chunk
-      const int gt = tid - kG0 * 32, cq = gt & 3;
+    if (warp >= kG0 && warp < kB0) {             // ---- gather: A tiles into tensor memory
+      // warp -> lane quarter q4 (rows 32 q4 .. 32 q4 + 31 of the M tile) and K16 half hk of each chunk
+      const int gt = tid - kG0 * 32, q4 = warp & 3, hk = (warp - kG0) >> 2;
       unsigned s = sc;
       for (int set = 0; set < 2; ++set) {
         const int nset = set ? nc : nv, n0 = set ? nv : 0;
@@ -372,103 +387,92 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
           }
           gather_bar();
           for (int mt = 0; mt < nmt; ++mt) {
-            // keys of this thread's two rows (G of the tile; keys may be negative)
-            int rkey[2];
-            bool rval[2];
-#pragma unroll
-            for (int it = 0; it < 2; ++it) {
-              const int row = mt * 128 + (gt >> 2) + it * 64;
-              rval[it] = row < MT;
-              rkey[it] = 0;
-              if (rval[it]) {
-                const char4 G = rows[row];
-                rkey[it] = ((int)G.x * g.by + (int)G.y) * g.bz + (int)G.z;
-              }
+            const int row = mt * 128 + q4 * 32 + lane;
+            const bool rval = row < MT;
+            int rkey = 0;
+            if (rval) {
+              const char4 G = rows[row];
+              rkey = ((int)G.x * g.by + (int)G.y) * g.bz + (int)G.z;
             }
             for (int c = 0; c < nch; ++c, ++s) {
-              const int st = (int)(s % (unsigned)g.stages);
+              const int sa = (int)(s & 1u);
               int ok = 1;
               if (lane == 0) {                   // warp-uniform decision
                 ok = *fail ? 0 : 1;
-                if (ok && s >= (unsigned)g.stages) {
-                  ok = mbar_wait(smem_u32(empty + st), ((s / g.stages) - 1) & 1u) ? 1 : 0;
+                if (ok && s >= (unsigned)kAStages) {
+                  ok = mbar_wait(smem_u32(empty_a + sa), ((s >> 1) - 1) & 1u) ? 1 : 0;
                   if (!ok) fail_now(fail, status);
                 }
               }
               ok = __shfl_sync(0xffffffffu, ok, 0);
               if (!ok) continue;
-              unsigned char* ah = sm + (size_t)st * g.stage_bytes;
-              unsigned char* al = ah + kTile;
-              // A: rows (gt >> 2) and (gt >> 2) + 64, K values 8 cq .. 8 cq + 7 of the chunk
-              const int4 ka = *reinterpret_cast<const int4*>(kkey + c * kTKC + cq * 8);
-              const int4 kb = *reinterpret_cast<const int4*>(kkey + c * kTKC + cq * 8 + 4);
-              const int kk8[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              uint32_t v[32];
+              if (rval) {
+                const int4* kp = reinterpret_cast<const int4*>(kkey + c * kTKC + hk * 16);
+                int kk16[16];
 #pragma unroll
-              for (int it = 0; it < 2; ++it) {
-                if (!rval[it]) continue;
-                const int i = (gt >> 2) + it * 64;
-                uint2 v[8];
+                for (int q = 0; q < 4; ++q) {
+                  const int4 t = kp[q];
+                  kk16[4 * q] = t.x;
+                  kk16[4 * q + 1] = t.y;
+                  kk16[4 * q + 2] = t.z;
+                  kk16[4 * q + 3] = t.w;
+                }
+                uint2 x[16];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = kcoef[bbox[kk8[e] - rkey[it]]];
-                uint4 rh, rl, ih, il;
-                rh.x = __byte_perm(v[0].x, v[1].x, 0x5410); rl.x = __byte_perm(v[0].x, v[1].x, 0x7632);
-                rh.y = __byte_perm(v[2].x, v[3].x, 0x5410); rl.y = __byte_perm(v[2].x, v[3].x, 0x7632);
-                rh.z = __byte_perm(v[4].x, v[5].x, 0x5410); rl.z = __byte_perm(v[4].x, v[5].x, 0x7632);
-                rh.w = __byte_perm(v[6].x, v[7].x, 0x5410); rl.w = __byte_perm(v[6].x, v[7].x, 0x7632);
-                ih.x = __byte_perm(v[0].y, v[1].y, 0x5410); il.x = __byte_perm(v[0].y, v[1].y, 0x7632);
-                ih.y = __byte_perm(v[2].y, v[3].y, 0x5410); il.y = __byte_perm(v[2].y, v[3].y, 0x7632);
-                ih.z = __byte_perm(v[4].y, v[5].y, 0x5410); il.z = __byte_perm(v[4].y, v[5].y, 0x7632);
-                ih.w = __byte_perm(v[6].y, v[7].y, 0x5410); il.w = __byte_perm(v[6].y, v[7].y, 0x7632);
-                *reinterpret_cast<uint4*>(ah + swz(i, cq)) = rh;
-                *reinterpret_cast<uint4*>(ah + swz(i, 4 + cq)) = ih;
-                *reinterpret_cast<uint4*>(al + swz(i, cq)) = rl;
-                *reinterpret_cast<uint4*>(al + swz(i, 4 + cq)) = il;
+                for (int e = 0; e < 16; ++e) x[e] = kcoef[bbox[kk16[e] - rkey]];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  v[j] = __byte_perm(x[2 * j].x, x[2 * j + 1].x, 0x5410);        // Re hi
+                  v[8 + j] = __byte_perm(x[2 * j].y, x[2 * j + 1].y, 0x5410);    // Im hi
+                  v[16 + j] = __byte_perm(x[2 * j].x, x[2 * j + 1].x, 0x7632);   // Re lo
+                  v[24 + j] = __byte_perm(x[2 * j].y, x[2 * j + 1].y, 0x7632);   // Im lo
+                }
+              } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = 0u;
               }
-              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+              umma::tmem_st32(tmem + ((uint32_t)(q4 * 32) << 16) + a_col0 + (uint32_t)(sa * kACols + hk * 32), v);
+              asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+              asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
               __syncwarp();
-              if (lane == 0) mbar_arrive(smem_u32(full + st));
+              if (lane == 0) mbar_arrive(smem_u32(full_a + sa));
             }
           }
         }
       }
-    } else if (warp == kB0) {                    // ---- B producer: two bulk copies per block (hi, lo rows)
+    } else if (warp == kB0) {                    // ---- B producer: the region's panel, two bulk copies per stage
       unsigned s = sc;
       for (int set = 0; set < 2; ++set) {
         const int nset = set ? nc : nv;
-        const uint32_t bytes = (uint32_t)(nblk * nset) * kImgRow, gbytes = (uint32_t)nset * umma::kRow;
+        const uint32_t half_bytes = (uint32_t)(rs * nset) * umma::kRow;
         for (int nn = 0; nn < nset; ++nn)
           for (int mt = 0; mt < nmt; ++mt)
             for (int c = 0; c < nch; ++c, ++s) {
+              if (lane != 0) continue;
               const int st = (int)(s % (unsigned)g.stages);
-              int ok = 1;
-              if (lane == 0) {
-                ok = *fail ? 0 : 1;
-                if (ok && s >= (unsigned)g.stages) {
-                  ok = mbar_wait(smem_u32(empty + st), ((s / g.stages) - 1) & 1u) ? 1 : 0;
-                  if (!ok) fail_now(fail, status);
-                }
-                if (ok) umma::mbar_arrive_expect_tx(smem_u32(full + st), bytes);
+              if (*fail) continue;
+              if (s >= (unsigned)g.stages && !mbar_wait(smem_u32(empty_b + st), ((s / g.stages) - 1) & 1u)) {
+                fail_now(fail, status);
+                continue;
               }
-              ok = __shfl_sync(0xffffffffu, ok, 0);
-              if (!ok) continue;
-              const uint32_t bh = smem_u32(sm + (size_t)st * g.stage_bytes + 2 * kTile);
-              const uint32_t bl = bh + (uint32_t)(g.nmax * umma::kRow);
-              for (int b = lane; b < nblk; b += 32) {
-                const int r0 = b * nset;
-                const unsigned char* p = bimg + group_off(d, binfo[b].y, set, c, r0 & 7, g.nkc);
-                umma::bulk_g2s(bh + (uint32_t)r0 * umma::kRow, p, gbytes, smem_u32(full + st));
-                umma::bulk_g2s(bl + (uint32_t)r0 * umma::kRow, p + gbytes, gbytes, smem_u32(full + st));
-              }
+              umma::mbar_arrive_expect_tx(smem_u32(full_b + st), 2 * half_bytes);
+              const uint32_t bh = smem_u32(sm + (size_t)st * g.stage_bytes);
+              const unsigned char* p = bimg + panel_off(d, r, set, c, g.nkc);
+              umma::bulk_g2s(bh, p, half_bytes, smem_u32(full_b + st));
+              umma::bulk_g2s(bh + (uint32_t)(g.nmax * umma::kRow), p + half_bytes, half_bytes, smem_u32(full_b + st));
             }
       }
     } else if (warp == kMmaWarp) {               // ---- MMA issue
       if (lane == 0) {
         unsigned s = sc, p = pc;
         bool ok = !*fail;
-        const uint64_t dstage0 = umma::smem_desc(smem_u32(sm));     // stage st: + st stage_bytes / 16
+        const uint64_t dstage0 = umma::smem_desc(smem_u32(sm));     // B stage st: + st stage_bytes / 16
+        const uint32_t blo = (uint32_t)((g.nmax * umma::kRow) >> 4);
         for (int set = 0; set < 2; ++set) {
           const int nset = set ? nc : nv;
-          const int N = (nblk * nset + 15) & ~15;
+          const int N = (rs * nset + 15) & ~15;
           const uint32_t idesc = umma::idesc_of(N);
           for (int nn = 0; nn < nset; ++nn)
             for (int mt = 0; mt < nmt; ++mt, ++p) {
@@ -478,25 +482,27 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
                 ok = false;
               }
               if (ok) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              const uint32_t d_re = tmem + (uint32_t)(buf * kAcc), d_im = d_re + 128;
+              const uint32_t d_re = tmem + (uint32_t)buf * acc_cols, d_im = d_re + half;
               for (int c = 0; c < nch; ++c, ++s) {
                 if (!ok || *fail) {
                   ok = false;
                   continue;
                 }
-                const int st = (int)(s % (unsigned)g.stages);
-                if (!mbar_wait(smem_u32(full + st), (s / g.stages) & 1u) || *fail) {
+                const int st = (int)(s % (unsigned)g.stages), sa = (int)(s & 1u);
+                if (!mbar_wait(smem_u32(full_a + sa), (s >> 1) & 1u) ||
+                    !mbar_wait(smem_u32(full_b + st), (s / g.stages) & 1u) || *fail) {
                   fail_now(fail, status);
                   ok = false;
                   continue;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t da = dstage0 + (uint64_t)((st * g.stage_bytes) >> 4), db = da + (uint64_t)((2 * kTile) >> 4);
-                const uint32_t lob = (uint32_t)((g.nmax * umma::kRow) >> 4);
+                const uint64_t db = dstage0 + (uint64_t)((st * g.stage_bytes) >> 4);
+                const uint32_t a = tmem + a_col0 + (uint32_t)(sa * kACols);
                 const int nkk = (kc - c * kTKC > 16) ? 2 : 1;
                 for (int kk = 0; kk < nkk; ++kk)
-                  umma::mma_cplx_k16_desc(d_re, d_im, da, kTile >> 4, db, lob, kk, idesc, c == 0 && kk == 0);
-                mma_commit(smem_u32(empty + st));
+                  umma::mma_cplx_k16_ts(d_re, d_im, a + (uint32_t)(kk * 32), db, blo, kk, idesc, c == 0 && kk == 0);
+                mma_commit(smem_u32(empty_a + sa));
+                mma_commit(smem_u32(empty_b + st));
               }
               if (ok) mma_commit(smem_u32(tfull + buf));
             }
@@ -508,7 +514,7 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
       short* pt = ptab + (size_t)(warp * 32 + lane) * rs;
       for (int set = 0; set < 2; ++set) {
         const int nset = set ? nc : nv;
-        const int ncols = nblk * nset;
+        const int ncols = rs * nset;
         for (int nn = 0; nn < nset; ++nn)
           for (int mt = 0; mt < nmt; ++mt, ++p) {
             const int buf = (int)(p & 1u);
@@ -518,11 +524,11 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
             if (valid) {
               const char4 G = rows[row];
 #pragma unroll 4
-              for (int b = 0; b < nblk; ++b) {
+              for (int b = 0; b < rs; ++b) {
                 const int4 bi = binfo[b];
                 const int x = G.x + (bi.z & 3) - 1, y = G.y + ((bi.z >> 2) & 3) - 1, z = G.z + ((bi.z >> 4) & 3) - 1;
                 short pb = -1;
-                if (x >= -f0 && x <= f0 && y >= -f1 && y <= f1 && z >= -f2 && z <= f2)
+                if (bi.x >= 0 && x >= -f0 && x <= f0 && y >= -f1 && y <= f1 && z >= -f2 && z <= f2)
                   pb = d.tc_pmap[(size_t)bi.x * pq + ((size_t)(x + f0) * kb1 + y + f1) * kb2 + z + f2];
                 pt[b] = pb;
               }
@@ -537,9 +543,9 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int c0 = 0; c0 < ncols; c0 += 32) {
               uint32_t v[32], u[32];
-              const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kAcc + c0);
+              const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)buf * acc_cols + (uint32_t)c0;
               umma::tmem_ld32(taddr, v);
-              umma::tmem_ld32(taddr + 128u, u);
+              umma::tmem_ld32(taddr + half, u);
               asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
               if (!valid) continue;
               int b = c0 / nset, m = c0 - b * nset;
@@ -577,7 +583,7 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
   if (warp == 0) {
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kAcc) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
 }
 
@@ -635,7 +641,7 @@ struct TpWs {
 TpWs tp_ws(const DevSys& d) {
   TpWs w;
   size_t o = 0;
-  w.bimg = o; o += ((size_t)d.nkpt * d.nb * (d.tc_kpad / kTKC) * 8 * kImgRow + 255) & ~(size_t)255;
+  w.bimg = o; o += ((size_t)d.nkpt * d.nb * (d.tc_kpad / kTKC) * kImgRow + 255) & ~(size_t)255;
   w.blist = o; o += ((size_t)d.nkpt * d.tc_nreg * d.tc_rsize * sizeof(int) + 255) & ~(size_t)255;
   w.counter = o; o += 256;
   w.total = o;
@@ -646,7 +652,7 @@ TpWs tp_ws(const DevSys& d) {
 
 // The tensor-core route needs a region of at most one N tile of columns and its tiles in shared memory.
 int tcpair_valid(const DevSys& d) {
-  if (d.tc_kpad < kTKC || d.tc_rsize < 1 || d.tc_rsize * (d.nv > d.nc ? d.nv : d.nc) > 128) return 0;
+  if (d.tc_kpad < kTKC || d.tc_rsize < 1 || d.tc_rsize * (d.nv > d.nc ? d.nv : d.nc) > 96) return 0;
   if (d.tc_rsize > kThreads) return 0;
   return stages_of(d) > 0 ? 1 : 0;
 }

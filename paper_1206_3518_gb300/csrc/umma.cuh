@@ -114,6 +114,45 @@ __device__ __forceinline__ void mma_cplx_k16_desc(uint32_t d_re, uint32_t d_im, 
   }
 }
 
+// A from tensor memory (column address a of lane 0), B from shared memory.
+__device__ __forceinline__ void mma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// The twelve MMAs of 16 complex K values with the A planes in tensor memory at columns a + 0 (Re hi),
+// a + 8 (Im hi), a + 16 (Re lo), a + 24 (Im lo) (two BF16 per 32-bit column, lane = row), B in shared
+// memory as for mma_cplx_k16_desc.
+__device__ __forceinline__ void mma_cplx_k16_ts(uint32_t d_re, uint32_t d_im, uint32_t a, uint64_t db, uint32_t b_lo,
+                                                int kk, uint32_t idesc, bool init) {
+  const uint32_t idesc_neg = idesc | kNegA;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {                 // hi.hi, hi.lo, lo.hi
+    const uint32_t ar = a + ((s == 2) ? 16u : 0u), ai = ar + 8u;
+    const uint64_t pb = db + ((s == 1) ? b_lo : 0u) + (uint32_t)kk * 2u;
+    const uint32_t acc = (init && s == 0) ? 0u : 1u;
+    mma_bf16_ts(d_re, ar, pb, idesc, acc);              // Re A Re B
+    mma_bf16_ts(d_re, ai, pb + 4u, idesc_neg, 1u);      // - Im A Im B
+    mma_bf16_ts(d_im, ar, pb + 4u, idesc, acc);         // Re A Im B
+    mma_bf16_ts(d_im, ai, pb, idesc, 1u);               // Im A Re B
+  }
+}
+
+// 32 consecutive TMEM columns of this warp's lane quarter from registers.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }

@@ -122,7 +122,7 @@ def test_chunking_does_not_change_the_densities(bse, cfg1):
 
 
 def test_fcc8_sampled_blocks_full_size(bse):
-    """fcc 8x8x8 3v4c at full size (regions of 1 x 4 x 8 k'): a seeded sample of 400 upper blocks of every
+    """fcc 8x8x8 3v4c at full size (regions of the plan's shape): a seeded sample of 400 upper blocks of every
     chunk of the bench's launch configuration against the oracle."""
     from paper_1206_3518_gb300.pipeline import Forward
     spec = config_spec("fcc_8x8x8_3v4c")
