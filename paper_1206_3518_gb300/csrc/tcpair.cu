@@ -27,9 +27,10 @@
 // tcpair_kernel is persistent (one CTA per SM) and takes tiles (k, region) from a counter, region-major.
 // Warps 0-3 drain the accumulators, warp 4 issues the MMAs (12 per 16 complex K, A from tensor memory,
 // B from shared memory), warps 5-12 gather the A tile of each K chunk (32 complex K values) straight into
-// tensor memory (two A slots, tcgen05.st), and warp 13 brings the B rows into a ring of shared-memory
-// stages with bulk copies (the region's panel of the chunk: its hi rows and its lo rows, counted on the
-// stage's mbarrier); the columns of a region's points without a block in the tile are computed and dropped.
+// tensor memory (two A slots, tcgen05.st; warps 5-8 the even stages, 9-12 the odd ones), and warp 13
+// brings the B rows into a ring of shared-memory stages with bulk copies (the region's panel of the chunk:
+// its hi rows and its lo rows, counted on the stage's mbarrier); the columns of a region's points without
+// a block in the tile are computed and dropped.
 // Two accumulators (Re | Im, 2 N <= 192 TMEM columns each) alternate between passes (one band n, 128
 // rows), so the epilogue of one pass overlaps the MMAs of the next.  Every mbarrier wait is bounded (2 s); on expiry the CTA
 // records BSE_ERR_TIMEOUT, stops issuing, waits (bounded) for its MMAs in flight, frees its tensor
@@ -233,7 +234,7 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
       mbar_init(smem_u32(empty_b + i), 1);
     }
     for (int i = 0; i < kAStages; ++i) {
-      mbar_init(smem_u32(full_a + i), kGWarps);
+      mbar_init(smem_u32(full_a + i), kGWarps / kAStages);
       mbar_init(smem_u32(empty_a + i), 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -366,8 +367,10 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
     const int nch = (kc + kTKC - 1) / kTKC;
 
     if (warp >= kG0 && warp < kB0) {             // ---- gather: A tiles into tensor memory
-      // warp -> lane quarter q4 (rows 32 q4 .. 32 q4 + 31 of the M tile) and K16 half hk of each chunk
-      const int gt = tid - kG0 * 32, q4 = warp & 3, hk = (warp - kG0) >> 2;
+      // warp -> lane quarter q4 (rows 32 q4 .. 32 q4 + 31 of the M tile) and A slot sa: the four warps of
+      // slot sa write every other stage, all 32 K values, in two halves (the first store overlaps the
+      // second half's lookups)
+      const int gt = tid - kG0 * 32, q4 = warp & 3, sa = (warp - kG0) >> 2;
       unsigned s = sc;
       for (int set = 0; set < 2; ++set) {
         const int nset = set ? nc : nv, n0 = set ? nv : 0;
@@ -395,7 +398,7 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
               rkey = ((int)G.x * g.by + (int)G.y) * g.bz + (int)G.z;
             }
             for (int c = 0; c < nch; ++c, ++s) {
-              const int sa = (int)(s & 1u);
+              if ((int)(s & 1u) != sa) continue;
               int ok = 1;
               if (lane == 0) {                   // warp-uniform decision
                 ok = *fail ? 0 : 1;
@@ -407,33 +410,36 @@ __global__ __launch_bounds__(kThreads, 1) void tcpair_kernel(DevSys d, const flo
               ok = __shfl_sync(0xffffffffu, ok, 0);
               if (!ok) continue;
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              uint32_t v[32];
-              if (rval) {
-                const int4* kp = reinterpret_cast<const int4*>(kkey + c * kTKC + hk * 16);
-                int kk16[16];
+#pragma unroll 1
+              for (int hk = 0; hk < 2; ++hk) {
+                uint32_t v[32];
+                if (rval) {
+                  const int4* kp = reinterpret_cast<const int4*>(kkey + c * kTKC + hk * 16);
+                  int kk16[16];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  const int4 t = kp[q];
-                  kk16[4 * q] = t.x;
-                  kk16[4 * q + 1] = t.y;
-                  kk16[4 * q + 2] = t.z;
-                  kk16[4 * q + 3] = t.w;
+                  for (int q = 0; q < 4; ++q) {
+                    const int4 t = kp[q];
+                    kk16[4 * q] = t.x;
+                    kk16[4 * q + 1] = t.y;
+                    kk16[4 * q + 2] = t.z;
+                    kk16[4 * q + 3] = t.w;
+                  }
+                  uint2 x[16];
+#pragma unroll
+                  for (int e = 0; e < 16; ++e) x[e] = kcoef[bbox[kk16[e] - rkey]];
+#pragma unroll
+                  for (int j = 0; j < 8; ++j) {
+                    v[j] = __byte_perm(x[2 * j].x, x[2 * j + 1].x, 0x5410);        // Re hi
+                    v[8 + j] = __byte_perm(x[2 * j].y, x[2 * j + 1].y, 0x5410);    // Im hi
+                    v[16 + j] = __byte_perm(x[2 * j].x, x[2 * j + 1].x, 0x7632);   // Re lo
+                    v[24 + j] = __byte_perm(x[2 * j].y, x[2 * j + 1].y, 0x7632);   // Im lo
+                  }
+                } else {
+#pragma unroll
+                  for (int j = 0; j < 32; ++j) v[j] = 0u;
                 }
-                uint2 x[16];
-#pragma unroll
-                for (int e = 0; e < 16; ++e) x[e] = kcoef[bbox[kk16[e] - rkey]];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                  v[j] = __byte_perm(x[2 * j].x, x[2 * j + 1].x, 0x5410);        // Re hi
-                  v[8 + j] = __byte_perm(x[2 * j].y, x[2 * j + 1].y, 0x5410);    // Im hi
-                  v[16 + j] = __byte_perm(x[2 * j].x, x[2 * j + 1].x, 0x7632);   // Re lo
-                  v[24 + j] = __byte_perm(x[2 * j].y, x[2 * j + 1].y, 0x7632);   // Im lo
-                }
-              } else {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = 0u;
+                umma::tmem_st32(tmem + ((uint32_t)(q4 * 32) << 16) + a_col0 + (uint32_t)(sa * kACols + hk * 32), v);
               }
-              umma::tmem_st32(tmem + ((uint32_t)(q4 * 32) << 16) + a_col0 + (uint32_t)(sa * kACols + hk * 32), v);
               asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
               asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
               __syncwarp();
