@@ -867,6 +867,21 @@ GCORR_TRAFFIC = {"sha1": "98a94e850b910092ba14723d028b70a6dc285429", "bytes_per_
                  "shape": ("fcc", 4, 4, 12.0)}
 
 
+# The same for the tensor-core route's kernel (tcpair_kernel): one ncu capture (--set full, one launch) of
+# the fcc 12x12x12 4v4c block shape on a 6x6x6 k mesh, q 54..108: 8,424 blocks, 281.7 MB read and 1262.9 MB
+# written (the densities at their sphere positions; the region panels of B mostly from L2).  Valid only for
+# the sources with this SHA-1 (tcpair.cu + umma.cuh) and that block shape.
+TCPAIR_TRAFFIC = {"sha1": "c9f94b9792c58bfbc62d27177708595c929ff119", "bytes_per_block": 183353.5,
+                  "shape": ("fcc", 4, 4, 12.0)}
+
+
+def _tcpair_sources_sha1():
+    import hashlib
+    base = os.path.join(ROOT, "paper_1206_3518_gb300", "csrc")
+    data = open(os.path.join(base, "tcpair.cu"), "rb").read() + open(os.path.join(base, "umma.cuh"), "rb").read()
+    return hashlib.sha1(data).hexdigest()
+
+
 def _gcorr_sources_sha1():
     import hashlib
     base = os.path.join(ROOT, "paper_1206_3518_gb300", "csrc")
@@ -907,6 +922,8 @@ def stage_rooflines(st, spec, inf, peaks, src, nchunks, pw, prec):
     if prec != 0 and pw.get("tensor"):
         useful = 24.0 * pw["cmac"]
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        same = (TCPAIR_TRAFFIC["shape"] == (spec.lattice, spec.nv, spec.nc, spec.ecut)
+                and TCPAIR_TRAFFIC["sha1"] == _tcpair_sources_sha1())
         out["pair_direct"] = {
             "bound": "tensor", "kernel": "tcpair_kernel", "achieved": useful / (ms / 1e3) / 1e12, "peak": peak,
             "unit": "TFLOP/s", "frac": useful / (ms / 1e3) / 1e12 / peak, "launches_per_step": 3 * nchunks + 1,
@@ -914,7 +931,8 @@ def stage_rooflines(st, spec, inf, peaks, src, nchunks, pw, prec):
                     "complex multiply-add, sum over upper blocks of NG(q) |S(k')| (Nv^2 + Nc^2) (the padding of "
                     "a tile's rows and K positions to the union of its spheres is not counted); the stage's "
                     "whole time (image packing and tile table included)",
-            "traffic": None, "peak_source": src + " (sustained bf16: timed inside a long step)"}
+            "traffic": TCPAIR_TRAFFIC["bytes_per_block"] * nb / nchunks if same else None,
+            "peak_source": src + " (sustained bf16: timed inside a long step)"}
     elif pw["method"] == "correlation":
         flops = 8.0 * pw["cmac"]
         same = (GCORR_TRAFFIC["shape"] == (spec.lattice, spec.nv, spec.nc, spec.ecut)
