@@ -151,11 +151,15 @@ def make_inputs(name):
     return spec, s
 
 
-def auto_qchunk(plan, nq, budget_bytes):
-    """Fewest q chunks whose direct pair densities and W.rho workspace fit in budget_bytes."""
+def auto_qchunk(plan, nq, budget_bytes, align=1):
+    """Fewest q chunks whose direct pair densities and W.rho workspace fit in budget_bytes; with align > 1
+    the chunk is rounded down to a multiple of align (whole planes of the q mesh, so that the tensor-core
+    pair route sees whole planes of k' for every k and fills its regions)."""
     from paper_1206_3518_gb300 import bse
     for n in range(1, nq + 1):
         ch = -(-nq // n)
+        if align > 1 and ch > align:
+            ch = ch // align * align
         chunks = [(q, min(q + ch, nq)) for q in range(0, nq, ch)]
         rho = max(bse.bse_rho_dir_count(plan, 0, a, b) for a, b in chunks) * plan.info(0)["ng_max"] * 8
         ws = bse.bse_workspace_size(plan, 0, bse.BSE_WS_KERNEL, ch)
@@ -279,7 +283,8 @@ def run_ours(args):
     free, _ = torch.cuda.mem_get_info(dev)
     fixed = (bse.bse_workspace_size(plan, 0, bse.BSE_WS_PAIR) + 2 * dim * dim * 8
              + inf["nq"] * inf["ng_max"] ** 2 * 8 * 2)
-    qchunk = args.qchunk or auto_qchunk(plan, inf["nq"], int(0.6 * (free - fixed)))
+    plane = spec.nk[1] * spec.nk[2] if inf["tensor_pair"] else 1
+    qchunk = args.qchunk or auto_qchunk(plan, inf["nq"], int(0.6 * (free - fixed)), plane)
     F = Forward(plan, 0, nsteps=spec.nsteps, nw=spec.nw, qchunk=qchunk)
     coef_h = torch.as_tensor(s.coef.astype(np.complex64)).pin_memory()
     en_h = torch.as_tensor(s.energies).pin_memory()

@@ -152,7 +152,8 @@ def _full_size_case(bse, name, frac, seed, eps_tol_fp32, eps_tol_mixed, k_tol_fp
         free, _ = torch.cuda.mem_get_info()
         fixed = (bse.bse_workspace_size(plan, 0, bse.BSE_WS_PAIR) + 3 * spec.dim * spec.dim * 8
                  + inf["nq"] * inf["ng_max"] ** 2 * 8 * 2)
-        qchunk = bench.auto_qchunk(plan, inf["nq"], int(0.5 * (free - fixed)))
+        plane = spec.nk[1] * spec.nk[2] if inf["tensor_pair"] else 1
+        qchunk = bench.auto_qchunk(plan, inf["nq"], int(0.5 * (free - fixed)), plane)
         F = Forward(plan, 0, nsteps=spec.nsteps, nw=spec.nw, qchunk=qchunk)
         coef, en, W = _dev(s.coef, torch.complex64), _dev(s.energies, torch.float64), _dev(s.W, torch.complex64)
         om = _dev(s.omega, torch.float64)
