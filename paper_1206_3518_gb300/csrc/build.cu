@@ -168,17 +168,25 @@ __global__ __launch_bounds__(wr::kThreads, 2) void gemm_wr(DevSys d, const float
 }
 
 constexpr int kBlkThreads = 256, KC = 32;
+constexpr int kBlkPerCta = 4, kBlkT = kBlkThreads / kBlkPerCta;   // block_kernel: 64 threads per block
 
 // Per upper block: M[a][c] = sum_G conj(L[a][G]) Rr[c][G], a = (v,v'), c = (c,c');
 // side V: L = X (= W R_v), Rr = R_c;  side C: L = R_v, Rr = X (= W R_c).
+// Four blocks per CTA, 64 threads per block, each thread a 2 x 2 patch of the (at most 16 x 16) product:
+// four shared-memory loads per four complex multiply-adds, sixteen global loads per thread in flight
+// per K step.
 __global__ __launch_bounds__(kBlkThreads) void block_kernel(DevSys d, const float2* __restrict__ rho_dir,
                                                            const float2* __restrict__ X, float2* __restrict__ H,
-                                                           int q_begin, long long vbase, int side_c) {
-  __shared__ float2 Ls[16][KC + 1];
-  __shared__ float2 Rs[16][KC + 1];
-  __shared__ float2 Bs[16][17];
+                                                           int q_begin, long long vbase, int side_c, long long b_count) {
+  __shared__ float2 Ls[kBlkPerCta][16][KC + 1];
+  __shared__ float2 Rs[kBlkPerCta][16][KC + 1];
+  __shared__ float2 Bs[kBlkPerCta][16][17];
+  __shared__ int ngs[kBlkPerCta];
+  const int grp = threadIdx.x / kBlkT, t = threadIdx.x % kBlkT;
+  const long long bi = (long long)blockIdx.x * kBlkPerCta + grp;
+  const bool live = bi < b_count;
   const long long b0 = d.qblk_off[q_begin];
-  const long long b = b0 + blockIdx.x;
+  const long long b = b0 + (live ? bi : 0);
   const int4 blk = d.blocks[b];
   const int k = blk.x, k2 = blk.y, q = blk.z;
   const long long qb = d.qblk_off[q];
@@ -192,54 +200,83 @@ __global__ __launch_bounds__(kBlkThreads) void block_kernel(DevSys d, const floa
   const float2* Xb = X + (size_t)((qb - b0 + local) * w) * d.ng_max;
   const float2* L = side_c ? Rv : Xb;
   const float2* R = side_c ? Xb : Rc;
-  const int NG = d.ngq[q];
-  const int t = threadIdx.x;
-  const int a = t / nc2, c = t % nc2;
-  const bool active = t < nv2 * nc2;
-  float2 acc = make_float2(0.f, 0.f);
-  for (int g0 = 0; g0 < NG; g0 += KC) {
-    for (int i = t; i < 16 * KC; i += kBlkThreads) {
+  const int NG = live ? d.ngq[q] : 0;
+  if (t == 0) ngs[grp] = NG;
+  __syncthreads();
+  int ngmax = 0;
+#pragma unroll
+  for (int i = 0; i < kBlkPerCta; ++i) ngmax = max(ngmax, ngs[i]);
+  const int i2 = t >> 3, j2 = t & 7;                 // rows a = 2 i2, 2 i2 + 1; columns c = 2 j2, 2 j2 + 1
+  float2 acc[2][2];
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int y = 0; y < 2; ++y) acc[x][y] = make_float2(0.f, 0.f);
+  for (int g0 = 0; g0 < ngmax; g0 += KC) {
+    for (int i = t; i < 16 * KC; i += kBlkT) {
       const int r = i / KC, g = i % KC;
       const bool in = (g0 + g) < NG;
-      Ls[r][g] = (r < nv2 && in) ? L[(size_t)r * d.ng_max + g0 + g] : make_float2(0.f, 0.f);
-      Rs[r][g] = (r < nc2 && in) ? R[(size_t)r * d.ng_max + g0 + g] : make_float2(0.f, 0.f);
+      Ls[grp][r][g] = (r < nv2 && in) ? L[(size_t)r * d.ng_max + g0 + g] : make_float2(0.f, 0.f);
+      Rs[grp][r][g] = (r < nc2 && in) ? R[(size_t)r * d.ng_max + g0 + g] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    if (active) {
 #pragma unroll 8
-      for (int g = 0; g < KC; ++g) {
-        const float2 l = Ls[a][g], r = Rs[c][g];
-        acc.x = fmaf(l.x, r.x, fmaf(l.y, r.y, acc.x));     // conj(l) r
-        acc.y = fmaf(l.x, r.y, fmaf(-l.y, r.x, acc.y));
-      }
+    for (int g = 0; g < KC; ++g) {
+      const float2 l0 = Ls[grp][2 * i2][g], l1 = Ls[grp][2 * i2 + 1][g];
+      const float2 r0 = Rs[grp][2 * j2][g], r1 = Rs[grp][2 * j2 + 1][g];
+      const float2 lv[2] = {l0, l1}, rv[2] = {r0, r1};
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+          acc[x][y].x = fmaf(lv[x].x, rv[y].x, fmaf(lv[x].y, rv[y].y, acc[x][y].x));     // conj(l) r
+          acc[x][y].y = fmaf(lv[x].x, rv[y].y, fmaf(-lv[x].y, rv[y].x, acc[x][y].y));
+        }
     }
     __syncthreads();
   }
   const int nv = d.nv, nc = d.nc, nvc = nv * nc;
   const float nrm = (float)d.norm;
-  int row = 0, col = 0;
-  float2 val = make_float2(0.f, 0.f);
-  if (active) {
-    const int v = a / nv, vp = a % nv, cc = c / nc, cp = c % nc;
-    row = v * nc + cc;                 // (k, v, c) local
-    col = vp * nc + cp;                // (k', v', c') local
-    const size_t hij = (size_t)(k * nvc + row) * d.dim + (size_t)k2 * nvc + col;
-    const float2 h = H[hij];
-    val = make_float2(h.x - nrm * acc.x, h.y - nrm * acc.y);
-    if (k != k2) {
-      H[hij] = val;
-      H[(size_t)(k2 * nvc + col) * d.dim + (size_t)k * nvc + row] = make_float2(val.x, -val.y);
-    } else {
-      Bs[row][col] = val;
+  int rows[2][2], colsv[2][2];
+  float2 vals[2][2];
+  bool act[2][2];
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int y = 0; y < 2; ++y) {
+      const int a = 2 * i2 + x, c = 2 * j2 + y;
+      act[x][y] = live && a < nv2 && c < nc2;
+      rows[x][y] = colsv[x][y] = 0;
+      vals[x][y] = make_float2(0.f, 0.f);
+      if (!act[x][y]) continue;
+      const int v = a / nv, vp = a % nv, cc = c / nc, cp = c % nc;
+      const int row = v * nc + cc;                 // (k, v, c) local
+      const int col = vp * nc + cp;                // (k', v', c') local
+      rows[x][y] = row;
+      colsv[x][y] = col;
+      const size_t hij = (size_t)(k * nvc + row) * d.dim + (size_t)k2 * nvc + col;
+      const float2 h = H[hij];
+      const float2 val = make_float2(h.x - nrm * acc[x][y].x, h.y - nrm * acc[x][y].y);
+      vals[x][y] = val;
+      if (k != k2) {
+        H[hij] = val;
+        H[(size_t)(k2 * nvc + col) * d.dim + (size_t)k * nvc + row] = make_float2(val.x, -val.y);
+      } else {
+        Bs[grp][row][col] = val;
+      }
     }
-  }
+  __syncthreads();
   if (k == k2) {
-    __syncthreads();
-    if (active) {
-      const float2 o = Bs[col][row];
-      H[(size_t)(k * nvc + row) * d.dim + (size_t)k * nvc + col] =
-          make_float2(0.5f * (val.x + o.x), 0.5f * (val.y - o.y));
-    }
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+      for (int y = 0; y < 2; ++y) {
+        if (!act[x][y]) continue;
+        const int row = rows[x][y], col = colsv[x][y];
+        const float2 o = Bs[grp][col][row];
+        H[(size_t)(k * nvc + row) * d.dim + (size_t)k * nvc + col] =
+            make_float2(0.5f * (vals[x][y].x + o.x), 0.5f * (vals[x][y].y - o.y));
+      }
   }
 }
 
@@ -487,8 +524,8 @@ int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin
   }
   if (e) return e;
   if (b_count > 0)
-    block_kernel<<<(unsigned)b_count, kBlkThreads, 0, st>>>(d, (const float2*)rho_dir, (const float2*)ws, (float2*)H,
-                                                            q_begin, vbase, side_c);
+    block_kernel<<<(unsigned)((b_count + kBlkPerCta - 1) / kBlkPerCta), kBlkThreads, 0, st>>>(
+        d, (const float2*)rho_dir, (const float2*)ws, (float2*)H, q_begin, vbase, side_c, b_count);
   return (int)cudaGetLastError();
 }
 
