@@ -192,7 +192,7 @@ class Step:
                                F.P, None, 0, 0, F.ws_pair)
         mark("realspace+exchange")
         bse.bse_build_kernel(plan, 0, bse.BSE_BK_INIT, F.rho_x, None, 0, 0, None, self.en, spec.delta, prec, F.H,
-                             None)
+                             F.ws_kernel if prec == bse.BSE_PREC_BF16X3 else None)
         mark("exchange_kernel")
         fdir = bse.BSE_PD_DIRECT | (bse.BSE_PD_TENSOR if self.tensor_pair(prec) else 0)
         for q0, q1 in F.chunks:

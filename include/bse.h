@@ -226,7 +226,11 @@ bse_status bse_pair_densities(bse_plan* plan, int s, unsigned flags,
 /*
  * A3 - A5.  Hamiltonian in the TDA (Eq. kernel, Eqs. V_eh and W_SS):
  *   H = diag(e_ck + delta - e_vk) + 2 K^x - K^d.
- * BSE_BK_INIT writes diag + 2K^x on the upper block triangle (k <= k').
+ * BSE_BK_INIT writes diag + 2K^x on the upper block triangle (k <= k') (on 128 x 128 tiles: also the
+ * lower entries of the diagonal tiles, which DIRECT, MIRROR or SYMFILL then overwrite).  With
+ * BSE_PREC_BF16X3 and a workspace (ws, at least bse_workspace_size(BSE_WS_KERNEL) for any chunk)
+ * 2K^x = Y^H Y, Y = rho_x diag(sqrt(2 vbar/(Omega Nk))), is a BF16x3 tcgen05 Gram product; with
+ * ws = NULL it is FP32 on CUDA cores.
  * BSE_BK_DIRECT subtracts K^d for the upper blocks of q in [q_begin, q_end)
  * (rho_dir laid out as in bse_pair_densities for the same range) and writes the
  * mirrored lower block H_k'k = H_kk'^H; diagonal blocks become (B + B^H)/2.

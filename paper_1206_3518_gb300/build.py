@@ -21,7 +21,7 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["pair.cu", "build.cu", "haydock.cu", "adjoint.cu", "tc.cu", "screen.cu", "coupled.cu", "gcorr.cu", "ritz.cu", "sym.cu", "scan.cu", "tddft.cu", "eig.cu", "tcpair.cu"]
+CU_SOURCES = ["pair.cu", "build.cu", "haydock.cu", "adjoint.cu", "tc.cu", "screen.cu", "coupled.cu", "gcorr.cu", "ritz.cu", "sym.cu", "scan.cu", "tddft.cu", "eig.cu", "tcpair.cu", "tcgram.cu"]
 CPP_SOURCES = ["plan.cpp"]
 
 

@@ -475,9 +475,13 @@ static long long direct_width(const DevSys& d) {
   return (d.nv * d.nv <= d.nc * d.nc) ? d.nv * d.nv : d.nc * d.nc;
 }
 
+// The direct stage's W.rho rows and split images of a q chunk; at least the exchange stage's split images of
+// rho_x (BSE_BK_INIT with BSE_PREC_BF16X3).
 size_t kernel_ws_bytes(const DevSys& d, long long qchunk) {
   const long long w = direct_width(d);
-  return x_bytes(d, qchunk, w) + tc_split_bytes(d, qchunk, w);
+  const size_t direct = x_bytes(d, qchunk, w) + tc_split_bytes(d, qchunk, w);
+  const size_t init = gram_ws_bytes(d);
+  return direct > init ? direct : init;
 }
 
 // Coupling build: W.rho_cv' rows and split images of a q chunk, or (init) conj(rho_x(-G)) rows.

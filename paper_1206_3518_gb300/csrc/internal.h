@@ -107,6 +107,9 @@ int pair_variants(const DevSys& d, int* out, int cap);
 int pair_variant_current(const DevSys& d);
 
 int launch_kernel_init(const DevSys& d, const void* rho_x, const double* energies, double delta, void* H, void* stream);
+size_t gram_ws_bytes(const DevSys& d);
+int launch_kernel_init_tc(const DevSys& d, const void* rho_x, const double* energies, double delta, void* H,
+                          void* ws, int* status, void* stream);
 int launch_mirror(const DevSys& d, void* H, void* stream);
 int launch_symfill(const DevSys& d, void* H, void* stream);
 int launch_kernel_direct_range(const DevSys& d, const void* rho_dir, int q_begin, int q_end, long long b_begin,

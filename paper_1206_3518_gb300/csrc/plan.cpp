@@ -928,7 +928,12 @@ bse_status bse_build_kernel(bse_plan* plan, int s, unsigned flags, const void* r
   if (flags & BSE_BK_INIT) {
     if (!rho_x || !energies) return set_error(BSE_ERR_ARG, "init needs rho_x and energies");
     if ((st = scan_input(plan, energies, (long long)d.nkpt * d.nb, 8, stream)) != BSE_OK) return st;
-    if ((st = cuda_check(launch_kernel_init(d, rho_x, energies, delta, H, stream), "kernel init")) != BSE_OK)
+    if (prec == BSE_PREC_BF16X3 && ws) {          // the tensor-core Gram product, split images in ws
+      if (ws_bytes < gram_ws_bytes(d)) return set_error(BSE_ERR_WORKSPACE, "kernel workspace too small for init");
+      if ((st = cuda_check(launch_kernel_init_tc(d, rho_x, energies, delta, H, ws, plan->d_status, stream),
+                           "kernel init (tensor)")) != BSE_OK)
+        return st;
+    } else if ((st = cuda_check(launch_kernel_init(d, rho_x, energies, delta, H, stream), "kernel init")) != BSE_OK)
       return st;
   }
   if (flags & BSE_BK_DIRECT) {

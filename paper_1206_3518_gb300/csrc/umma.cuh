@@ -153,6 +153,23 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
       : "memory");
 }
 
+// The twelve MMAs of 16 complex K values for conj(A) B (descriptors as mma_cplx_k16_desc):
+//   Re D += Re A Re B + Im A Im B,   Im D += Re A Im B - Im A Re B.
+__device__ __forceinline__ void mma_cplx_conj_k16_desc(uint32_t d_re, uint32_t d_im, uint64_t da, uint32_t a_lo,
+                                                       uint64_t db, uint32_t b_lo, int kk, uint32_t idesc, bool init) {
+  const uint32_t idesc_neg = idesc | kNegA;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {                 // hi.hi, hi.lo, lo.hi
+    const uint64_t pa = da + ((s == 2) ? a_lo : 0u) + (uint32_t)kk * 2u;
+    const uint64_t pb = db + ((s == 1) ? b_lo : 0u) + (uint32_t)kk * 2u;
+    const uint32_t acc = (init && s == 0) ? 0u : 1u;
+    mma_bf16(d_re, pa, pb, idesc, acc);                 // Re A Re B
+    mma_bf16(d_re, pa + 4u, pb + 4u, idesc, 1u);        // + Im A Im B
+    mma_bf16(d_im, pa, pb + 4u, idesc, acc);            // Re A Im B
+    mma_bf16(d_im, pa + 4u, pb, idesc_neg, 1u);         // - Im A Re B
+  }
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }

@@ -58,7 +58,7 @@ class Forward:
         bse.bse_pair_densities(p, s, bse.BSE_PD_REALSPACE | bse.BSE_PD_EXCHANGE, coef, energies, self.rho_x, self.P,
                                None, 0, 0, self.ws_pair)
         bse.bse_build_kernel(p, s, bse.BSE_BK_INIT, self.rho_x, None, 0, 0, None, energies, delta, prec, self.H,
-                             None)
+                             self.ws_kernel if prec == bse.BSE_PREC_BF16X3 else None)
         for q0, q1 in self.chunks:
             bse.bse_pair_densities(p, s, fdir, None, None, None, None, self.rho_dir, q0, q1, self.ws_pair)
             bse.bse_build_kernel(p, s, bse.BSE_BK_DIRECT, None, self.rho_dir, q0, q1, W, None, delta, prec, self.H,
