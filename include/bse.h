@@ -273,8 +273,8 @@ bse_status bse_apply_H(bse_plan* plan, int s, const void* H, const void* X, void
  * (Eq. epsilon_chi_bar in the TDA, Appendix A resolvent).
  * omega float64 [nw] (Ha), eps2 float64 [nw], ab float64 [2*nsteps]
  * (a_0..a_{n-1}, then b_0 = 0, b_1..b_{n-1}), steps_done int32 [1]: fewer than
- * nsteps after a breakdown (b_{j+1} <= 1e-10 |H v_j|), which is exact, not an
- * error.  One persistent cooperative launch; device-side barrier waits are
+ * nsteps after a breakdown (b_{j+1} <= 1e-6 |H v_j|, the FP32 rounding level of
+ * the product), which is exact, not an error.  One persistent cooperative launch; device-side barrier waits are
  * bounded and report BSE_ERR_TIMEOUT through bse_status_read.
  */
 bse_status bse_spectrum(bse_plan* plan, int s, const void* H, const void* P, int nsteps,

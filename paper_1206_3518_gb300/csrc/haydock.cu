@@ -79,18 +79,18 @@ __device__ bool grid_barrier(unsigned* bar, int* status, unsigned gsize) {
       const unsigned long long t0 = globaltimer();
       unsigned it = 0;
       while (ld_acquire(gen) == g) {
-        __nanosleep(32);
-        if ((++it & 31u) == 0) {
+        if ((it++ & 31u) == 0) {             // the first poll and every 32nd: a zero limit expires at once
           if (*(volatile int*)status != 0) {
             good = 0;
             break;
           }
-          if (globaltimer() - t0 > g_wait_limit_ns) {
+          if (globaltimer() - t0 >= g_wait_limit_ns) {
             atomicCAS(status, 0, (int)BSE_ERR_TIMEOUT);
             good = 0;
             break;
           }
         }
+        __nanosleep(32);
       }
     }
     ok = good;
