@@ -178,6 +178,8 @@ class Step:
         self.launches = 0
 
     def __call__(self, prec, marks=None, w_ready=None, w_free=None):
+        """w_ready / w_free (end to end): per q chunk, the event after which that chunk's rows of W are on the
+        device, and the event this step records once its direct term has read them."""
         import torch
         from paper_1206_3518_gb300 import bse
         F, spec, plan = self.F, self.spec, self.plan
@@ -195,16 +197,16 @@ class Step:
                              F.ws_kernel if prec == bse.BSE_PREC_BF16X3 else None)
         mark("exchange_kernel")
         fdir = bse.BSE_PD_DIRECT | (bse.BSE_PD_TENSOR if self.tensor_pair(prec) else 0)
-        for q0, q1 in F.chunks:
+        for c, (q0, q1) in enumerate(F.chunks):
             bse.bse_pair_densities(plan, 0, fdir, None, None, None, None, F.rho_dir, q0, q1, F.ws_pair)
             mark("pair_direct")
             if w_ready is not None:
-                self.stream.wait_event(w_ready)
+                self.stream.wait_event(w_ready[c])
             bse.bse_build_kernel(plan, 0, bse.BSE_BK_DIRECT, None, F.rho_dir, q0, q1, self.W, None, spec.delta, prec,
                                  F.H, F.ws_kernel)
+            if w_free is not None:
+                w_free[c].record(self.stream)
             mark("direct_contract")
-        if w_free is not None:
-            w_free.record(self.stream)
         bse.bse_spectrum(plan, 0, F.H, F.P, spec.nsteps, self.om, spec.eta, F.eps2, F.ab, F.steps_done, F.ws_spec)
         mark("spectrum")
 
@@ -310,27 +312,32 @@ def run_ours(args):
     Hmx = F.H.cpu().numpy() if H32 is not None else None
 
     # end to end through host buffers at the headline (mixed) precision: inputs H2D from pinned memory and
-    # eps_2 D2H every step.  W (the largest input) is uploaded on a second stream while the pair densities run.
+    # eps_2 D2H every step.  W (the largest input) is uploaded on a second stream, one q chunk's rows at a
+    # time: chunk c's rows as soon as the previous step's direct term of chunk c has read them, and the
+    # direct term of chunk c waits for its own rows only.
     eps_host = torch.empty(spec.nw, dtype=torch.float64).pin_memory()
     h2d = coef_h.numel() * 8 + en_h.numel() * 8 + W_h.numel() * 8 + om_h.numel() * 8
     d2h = spec.nw * 8
     e_steps = max(1, min(args.steps, 3))
     side = torch.cuda.Stream()
-    w_free = torch.cuda.Event()
+    w_free = [torch.cuda.Event() for _ in F.chunks]
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    w_free.record(stream)
+    for ev in w_free:
+        ev.record(stream)
     for _ in range(e_steps):
         coef.copy_(coef_h, non_blocking=True)
         en.copy_(en_h, non_blocking=True)
         om.copy_(om_h, non_blocking=True)
-        side.wait_event(w_free)
-        with torch.cuda.stream(side):
-            W.copy_(W_h, non_blocking=True)
-        w_ready = torch.cuda.Event()
-        w_ready.record(side)
+        w_ready = []
+        for c, (q0, q1) in enumerate(F.chunks):
+            side.wait_event(w_free[c])
+            with torch.cuda.stream(side):
+                W[q0:q1].copy_(W_h[q0:q1], non_blocking=True)
+            w_ready.append(torch.cuda.Event())
+            w_ready[-1].record(side)
         step(MIXED, w_ready=w_ready, w_free=w_free)
         eps_host.copy_(F.eps2, non_blocking=True)
     e1.record(stream)
@@ -597,7 +604,8 @@ def run_symmetry(plan, inf, W, dev):
 
 
 def run_batch(args, dev, rank=0, world=1):
-    """Layered 2D batch: 16 hexagonal sheets (dims 576..20736), BF16x3 contractions, autotuned pair tiles,
+    """Layered 2D batch: 16 hexagonal sheets (dims 576..20736), BF16x3 contractions, autotuned pair tiles
+    (the tensor-core route of the direct densities among the candidates),
     per-system builds plus one batched persistent spectrum launch, the whole sequence replayed as one
     CUDA graph.  With several ranks the sheets are sharded (balanced by dim^2, no exchange) and the time
     is the slowest rank's.  Returns the summary for the JSON line."""
@@ -624,8 +632,8 @@ def run_batch(args, dev, rank=0, world=1):
     tuned = []
     for i, F in enumerate(B.sys):
         bse.bse_pair_densities(plan, i, bse.BSE_PD_REALSPACE, coefs[i], ens[i], None, None, None, 0, 0, F.ws_pair)
-        r = autotune.tune(plan, i, F)
-        tuned.append(r["variant"]["index"])
+        r = autotune.tune(plan, i, F, with_tensor=True)
+        tuned.append("tensor" if r.get("tensor") else r["variant"]["index"])
     prec = bse.BSE_PREC_BF16X3
 
     def seq():
@@ -874,10 +882,11 @@ GCORR_TRAFFIC = {"sha1": "98a94e850b910092ba14723d028b70a6dc285429", "bytes_per_
 
 
 # The same for the tensor-core route's kernel (tcpair_kernel): one ncu capture (--set full, one launch) of
-# the fcc 12x12x12 4v4c block shape on a 6x6x6 k mesh, q 54..108: 8,424 blocks, 281.7 MB read and 1262.9 MB
-# written (the densities at their sphere positions; the region panels of B mostly from L2).  Valid only for
-# the sources with this SHA-1 (tcpair.cu + umma.cuh) and that block shape.
-TCPAIR_TRAFFIC = {"sha1": "c9f94b9792c58bfbc62d27177708595c929ff119", "bytes_per_block": 183353.5,
+# the fcc 12x12x12 4v4c block shape on a 6x6x6 k mesh, q 72..144 (two whole planes of the q mesh, as the
+# bench's chunks are): 9,072 blocks, 357.2 MB read and 1415.1 MB written (the densities at their sphere
+# positions; the region panels of B mostly from L2).  Valid only for the sources with this SHA-1
+# (tcpair.cu + umma.cuh) and that block shape.
+TCPAIR_TRAFFIC = {"sha1": "44be08bd79adb79e5e4217dbf94880d38196fef7", "bytes_per_block": 195365.4,
                   "shape": ("fcc", 4, 4, 12.0)}
 
 

@@ -25,6 +25,7 @@ class Forward:
         self.info = inf
         self.dim, self.nq, self.ng_max = inf["dim"], inf["nq"], inf["ng_max"]
         self.nsteps = nsteps
+        self.tensor_choice = None             # set by autotune.tune(..., with_tensor=True)
         if keep_rho_dir or qchunk is None:
             qchunk = self.nq
         self.qchunk = qchunk
@@ -49,11 +50,13 @@ class Forward:
         """A1-A6: pair densities, dipole and H (direct term streamed over q chunks).
 
         tensor_pair: direct pair densities on the tensor cores (BSE_PD_TENSOR); by default with the
-        mixed precision where the system has that route.
+        mixed precision where the system has that route, or as the autotuner chose for this system.
         """
         p, s = self.plan, self.s
         if tensor_pair is None:
             tensor_pair = prec == bse.BSE_PREC_BF16X3 and bool(self.info["tensor_pair"])
+            if tensor_pair and self.tensor_choice is not None:
+                tensor_pair = self.tensor_choice
         fdir = bse.BSE_PD_DIRECT | (bse.BSE_PD_TENSOR if tensor_pair else 0)
         bse.bse_pair_densities(p, s, bse.BSE_PD_REALSPACE | bse.BSE_PD_EXCHANGE, coef, energies, self.rho_x, self.P,
                                None, 0, 0, self.ws_pair)

@@ -109,3 +109,28 @@ def test_autotune_picks_fastest_and_caches(bse, tmp_path):
     r2 = autotune.tune(plan2, 0, F, cache_path=cache)
     assert r2["cached"] and r2["variant"]["index"] == r["variant"]["index"]
     assert bse.bse_pair_variants(plan2, 0)[1] == r["variant"]["index"]
+
+
+def test_autotune_tensor_candidate(bse, tmp_path):
+    """For a mixed-precision build the tensor-core route is one more timed candidate: the faster of it and
+    the best variant is recorded on the Forward, which build() then follows, and the cache keeps it."""
+    from paper_1206_3518_gb300 import autotune
+    from paper_1206_3518_gb300.pipeline import Forward
+    spec = slab_batch_specs(0)[5].replace(name="tune_tc", nk=(24, 24, 1), nv=1, nc=2)
+    s = generate(spec, wdtype=np.complex64)
+    plan = bse.Plan([spec])
+    assert plan.info(0)["tensor_pair"] == 1
+    F = Forward(plan, 0, nsteps=10, nw=50, qchunk=48)
+    bse.bse_pair_densities(plan, 0, bse.BSE_PD_REALSPACE, _dev(s.coef, torch.complex64),
+                           _dev(s.energies, torch.float64), None, None, None, 0, 0, F.ws_pair)
+    cache = str(tmp_path / "tune.json")
+    r = autotune.tune(plan, 0, F, reps=2, cache_path=cache, with_tensor=True)
+    assert isinstance(r["tensor"], bool) and r["ms"]["tensor"] > 0
+    best_variant = r["ms"][str(r["variant"]["index"])]
+    assert r["tensor"] == (r["ms"]["tensor"] < best_variant)
+    assert F.tensor_choice == r["tensor"]
+    print(f"tensor route {r['ms']['tensor']:.3f} ms against variant {r['variant']['index']} {best_variant:.3f} ms: "
+          f"{'tensor' if r['tensor'] else 'variant'}")
+    F2 = Forward(plan, 0, nsteps=10, nw=50, qchunk=48)
+    r2 = autotune.tune(plan, 0, F2, cache_path=cache, with_tensor=True)
+    assert r2["cached"] and r2["tensor"] == r["tensor"] and F2.tensor_choice == r["tensor"]
