@@ -838,9 +838,10 @@ def run_stage(args):
                            F.ws_pair)
     q0, q1 = F.chunks[min(1, len(F.chunks) - 1)]
     prec = bse.BSE_PREC_BF16X3 if args.prec == "bf16x3" else bse.BSE_PREC_FP32
+    ws_init = F.ws_kernel if prec == bse.BSE_PREC_BF16X3 else None
     if args.only == "contract":
         bse.bse_pair_densities(plan, 0, bse.BSE_PD_DIRECT, None, None, None, None, F.rho_dir, q0, q1, F.ws_pair)
-        bse.bse_build_kernel(plan, 0, bse.BSE_BK_INIT, F.rho_x, None, 0, 0, None, en, spec.delta, prec, F.H, None)
+        bse.bse_build_kernel(plan, 0, bse.BSE_BK_INIT, F.rho_x, None, 0, 0, None, en, spec.delta, prec, F.H, ws_init)
 
     fdir = bse.BSE_PD_DIRECT | (bse.BSE_PD_TENSOR if prec == bse.BSE_PREC_BF16X3 and F.info["tensor_pair"] else 0)
 
@@ -850,6 +851,9 @@ def run_stage(args):
         elif args.only == "contract":
             bse.bse_build_kernel(plan, 0, bse.BSE_BK_DIRECT, None, F.rho_dir, q0, q1, W, None, spec.delta, prec, F.H,
                                  F.ws_kernel)
+        elif args.only == "exchange":
+            bse.bse_build_kernel(plan, 0, bse.BSE_BK_INIT, F.rho_x, None, 0, 0, None, en, spec.delta, prec, F.H,
+                                 ws_init)
         else:
             F.spectrum(om, spec.eta)
 
@@ -865,7 +869,8 @@ def run_stage(args):
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
     bse.bse_status_read(plan)
-    nblk = sum(len(bse.bse_pair_blocks(plan, 0, q)[0]) for q in range(q0, q1)) if args.only != "spectrum" else 0
+    nblk = (sum(len(bse.bse_pair_blocks(plan, 0, q)[0]) for q in range(q0, q1))
+            if args.only in ("pair", "contract") else 0)
     print(json.dumps({"stage": args.only, "config": spec.name, "ms": times, "q_range": [q0, q1], "blocks": nblk}))
 
 
@@ -1178,8 +1183,9 @@ def main():
     ap.add_argument("--no-symmetry", action="store_true", help="skip the q-point symmetry measurement")
     ap.add_argument("--no-tddft", action="store_true", help="skip the TDDFT macroscopic dielectric function")
     ap.add_argument("--no-states", action="store_true", help="skip the exciton-state eigensolver")
-    ap.add_argument("--only", default="all", choices=["all", "pair", "spectrum", "contract"],
+    ap.add_argument("--only", default="all", choices=["all", "pair", "spectrum", "contract", "exchange"],
                     help="profiling aid: run one stage (pair: realspace + a q chunk of pair densities; "
+                         "contract: the direct term of a q chunk; exchange: diagonal + 2 K^x; "
                          "spectrum: Haydock on an H built once before the loop)")
     ap.add_argument("--qchunk", type=int, default=0, help="q points per direct-term chunk (0 = automatic)")
     ap.add_argument("--variant", type=int, default=-1, help="profiling aid for --only pair: pair-kernel variant index")
