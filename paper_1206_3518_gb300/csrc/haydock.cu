@@ -108,16 +108,11 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
   return v;
 }
 
-// x loaders: FP32 vectors written by other CTAs inside the kernel bypass L1 (ld.cg);
-// FP64 inputs of bse_apply_H are read-only and rounded to FP32 on the fly.
-__device__ __forceinline__ float4 load_x2(const float2* x, int i) {
-  return __ldcg(reinterpret_cast<const float4*>(x) + i);
-}
+// x loaders of bse_apply_H: the FP64 inputs are read-only and rounded to FP32 on the fly.
 __device__ __forceinline__ float4 load_x2(const double2* x, int i) {
   const double2 a = __ldg(x + 2 * i), b = __ldg(x + 2 * i + 1);
   return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
 }
-__device__ __forceinline__ float2 load_x1(const float2* x, int i) { return __ldcg(x + i); }
 __device__ __forceinline__ float2 load_x1(const double2* x, int i) {
   const double2 a = __ldg(x + i);
   return make_float2((float)a.x, (float)a.y);
