@@ -875,14 +875,14 @@ def run_stage(args):
 
 
 
-# DRAM bytes (read + write) per upper block of the correlation kernel's direct set, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, one launch) of the fcc 12x12x12 4v4c block shape (Ecut 12,
-# 48^3 grid) on a 6x6x6 k mesh: 23,436 blocks (all 216 q) in one launch, 4.5 GB on the device, 159.7 MB read
-# and 2944.9 MB written.  A full launch of the workload processes nblocks / q_chunks blocks of the same shape
-# and the bytes grow with the blocks (the densities are written once, the coefficients are read from L2), so
-# the traffic per launch is this figure times the launch's blocks.  Valid only for the sources with this
-# SHA-1 (gcorr.cu + pairjob.cuh) and that block shape.
-GCORR_TRAFFIC = {"sha1": "98a94e850b910092ba14723d028b70a6dc285429", "bytes_per_block": 132469.9,
+# DRAM bytes (read + write) per upper block of the correlation kernel's direct set (the default schedule,
+# gcorr_kernel<4, 4, 1, 0>), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one launch) of
+# the fcc 12x12x12 4v4c block shape (Ecut 12, 48^3 grid) on a 6x6x6 k mesh: 23,436 blocks (all 216 q) in one
+# launch, 4.5 GB on the device, 155.8 MB read and 2939.5 MB written.  A full launch of the workload processes
+# nblocks / q_chunks blocks of the same shape and the bytes grow with the blocks (the densities are written
+# once, the coefficients are read from L2), so the traffic per launch is this figure times the launch's
+# blocks.  Valid only for the sources with this SHA-1 (gcorr.cu + pairjob.cuh) and that block shape.
+GCORR_TRAFFIC = {"sha1": "ebbbbf8406f12035e2778354e7d61fd0fc693ec8", "bytes_per_block": 132074.1,
                  "shape": ("fcc", 4, 4, 12.0)}
 
 
