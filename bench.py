@@ -382,6 +382,7 @@ def run_ours(args):
     }
     if H32 is not None:
         out["cpu_baseline"] = cpu_baseline(spec, s, H32, Hmx, e32, emx, steps32, budget_s=args.cpu_budget)
+        out["cpu_baseline"]["full_small"] = cpu_full_small()
         del H32, Hmx
 
     del F, step, coef, en, W, om, coef_h, W_h
@@ -1097,6 +1098,29 @@ def cpu_baseline(spec, s, H32, Hmx, eps32, epsmx, steps_done, budget_s=15.0):
                        "oracle_steps_done": int(done), "gpu_steps_done": int(steps_done),
                        "note": "kernel errors relative to the largest sampled kernel entry; eps_2 errors relative "
                                "to the oracle spectrum's peak"}}
+
+
+def cpu_full_small(runs=3):
+    """The oracle's whole step, unsampled, on the tiny bulk cell (fcc 4x4x4 3v3c, dim 576): every pair
+    density, the full H (exchange and direct terms) and its Haydock spectrum; the median over runs."""
+    import time as _t
+    import numpy as np
+    from oracle import kernel as ok, pair as op, spectrum as osp
+    from synth import config_spec, generate
+    spec = config_spec("fcc_4x4x4_3v3c")
+    s = generate(spec)
+    times = []
+    for _ in range(runs):
+        t0 = _t.perf_counter()
+        H = ok.hamiltonian_full(spec, s.gk, s.coef, s.energies, s.W, spec.delta)
+        P = op.dipole(spec, s.gk, s.coef, s.energies)
+        osp.eps2_haydock(spec, H, P, s.omega, spec.eta, spec.nsteps)
+        times.append(_t.perf_counter() - t0)
+    med = float(np.median(times))
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"workload": f"{spec.name}: dim {spec.dim}, {spec.nsteps} Haydock steps, {len(s.omega)} w, whole step",
+            "runs": runs, "median_s": med, "value": spec.dim * spec.dim / med, "unit": UNIT, "cores": cores,
+            "kind": "oracle"}
 
 
 def run_reference(args):
