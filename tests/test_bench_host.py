@@ -59,6 +59,35 @@ def test_auto_qchunk_fits_the_budget():
         assert rho2 + bse.bse_workspace_size(plan, 0, bse.BSE_WS_KERNEL, ch2) > budget
 
 
+def test_auto_qchunk_whole_planes():
+    """With align = a plane of the q mesh, chunks are whole planes (so every region of k' is full for each k)
+    whenever one plane fits the budget, and still fit it; a budget that holds one plane only gives one plane;
+    below that the chunks are smaller than a plane and fit."""
+    bse = pytest.importorskip("paper_1206_3518_gb300.bse")
+    try:
+        bse.load()
+    except RuntimeError:
+        pytest.skip("library not built")
+    bench = _bench()
+    spec = config_spec("fcc_8x8x8_3v4c")
+    plan = bse.Plan([spec], host_only=True)
+    nq = plan.info(0)["nq"]
+    plane = spec.nk[1] * spec.nk[2]
+
+    def need(ch):
+        chunks = [(q, min(q + ch, nq)) for q in range(0, nq, ch)]
+        rho = max(bse.bse_rho_dir_count(plan, 0, a, b) for a, b in chunks) * plan.info(0)["ng_max"] * 8
+        return rho + bse.bse_workspace_size(plan, 0, bse.BSE_WS_KERNEL, ch)
+
+    one = need(plane)
+    for budget in (6e9, 2.5 * one, one):
+        ch = bench.auto_qchunk(plan, nq, budget, plane)
+        assert ch % plane == 0 and need(ch) <= budget
+    assert bench.auto_qchunk(plan, nq, one, plane) == plane
+    ch = bench.auto_qchunk(plan, nq, 0.7 * one, plane)
+    assert ch < plane and need(ch) <= 0.7 * one
+
+
 def test_stage_rooflines_arithmetic():
     bench = _bench()
     spec = config_spec("fcc_12x12x12_4v4c")
